@@ -1,0 +1,173 @@
+"""CPU oracle for the twofold exp/log library -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA kernels and
+their C ABI) never calls it, and the two share no code: this side is plain C in
+IEEE binary128 (``tf_oracle.c``) plus an arbitrary-precision ``decimal``
+tie-breaker, written from the definition of a twofold function (paper,
+"Twofold exponent" > "Method summary"; "Twofold logarithm" > "Newton
+inversion"): z0 is f(x0) correctly rounded, z0 + z1 approximates f(x0 + x1).
+
+Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
+``tests/test_oracle.py`` (decimal evaluations at 60+ digits, closed forms,
+series, invariants and planted-mistake checks).
+"""
+from __future__ import annotations
+
+import ctypes
+import decimal
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+
+KINDS = {"texp": 0, "texpm1": 1, "tlog": 2, "tlog1p": 3, "tadd": 4, "tmul": 5}
+FL_AMBIG, FL_EXACT = 1, 2
+
+_lib = None
+_lock = threading.Lock()
+
+
+def _compile(out: str, defines=()) -> None:
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+            "-frounding-math", *[f"-D{d}" for d in defines], _SRC, "-o", out, "-lm"]
+    # OpenMP when the host compiler has it; the oracle is correct either way.
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True, text=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True, text=True)
+
+
+def build(force: bool = False, defines=(), name: str = "libtforacle.so") -> str:
+    """Compile tf_oracle.c into oracle/_build/<name>; returns the path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, name)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        _compile(out, defines)
+    return out
+
+
+def _bind(path: str):
+    lib = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.tfo_eval.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, dp, dp, dp, dp, dp, dp,
+                             ctypes.POINTER(ctypes.c_uint)]
+    lib.tfo_eval.restype = ctypes.c_int
+    lib.tfo_libq.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp]
+    lib.tfo_libq.restype = ctypes.c_int
+    lib.tfo_threads.restype = ctypes.c_int
+    lib.tfo_set_threads.argtypes = [ctypes.c_int]
+    return lib
+
+
+def load(path: str | None = None):
+    """The oracle library (built on first use)."""
+    global _lib
+    if path is not None:
+        return _bind(path)
+    with _lock:
+        if _lib is None:
+            _lib = _bind(build())
+    return _lib
+
+
+def threads() -> int:
+    return load().tfo_threads()
+
+
+def set_threads(t: int) -> None:
+    load().tfo_set_threads(int(t))
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _as_f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Result:
+    """Per-element oracle answer.
+
+    Z0     f(x0) rounded to nearest double (the required main part),
+    Gh+Gl  the ideal z1: F - Z0 with F = f(x0 + x1), to about 106 bits,
+    A      |F| rounded to double (scale of the relative error),
+    flags  FL_EXACT: the special-value rules fix z1 = Gh exactly.
+    """
+
+    def __init__(self, Z0, Gh, Gl, A, flags):
+        self.Z0, self.Gh, self.Gl, self.A, self.flags = Z0, Gh, Gl, A, flags
+
+
+def evaluate(func: str, x0, x1=None, y0=None, y1=None, lib=None) -> Result:
+    """Oracle answer for every element of the twofold function ``func``."""
+    lib = lib or load()
+    kind = KINDS[func]
+    x0, x1, y0, y1 = map(_as_f64, (x0, x1, y0, y1))
+    n = x0.shape[0]
+    Z0, Gh, Gl, A = (np.empty(n) for _ in range(4))
+    fl = np.empty(n, dtype=np.uint32)
+    rc = lib.tfo_eval(kind, n, _p(x0), _p(x1), _p(y0), _p(y1), _p(Z0), _p(Gh), _p(Gl), _p(A),
+                      fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint)))
+    if rc != 0:
+        raise ValueError(f"tfo_eval rejected its arguments ({rc})")
+    amb = np.nonzero(fl & FL_AMBIG)[0]
+    for i in amb:  # re-decide the rounding of f(x0) with 80 significant digits
+        if func in ("texp", "texpm1", "tlog", "tlog1p"):
+            z = round_to_double(dec_f(func, float(x0[i]), 80))
+            if z != Z0[i]:
+                Gh[i] -= z - Z0[i]  # both are within one double spacing: exact shift
+                Z0[i] = z
+    fl &= ~np.uint32(FL_AMBIG)
+    return Result(Z0, Gh, Gl, A, fl)
+
+
+def libq(func: str, x) -> np.ndarray:
+    """glibc binary128 f(x) as (n, 2) hi/lo doubles -- for pinning tests only."""
+    x = _as_f64(x)
+    out = np.empty((x.shape[0], 2))
+    load().tfo_libq(KINDS[func], x.shape[0], _p(x), _p(out))
+    return out
+
+
+# ---------------------------------------------------------------------------------
+# Arbitrary-precision decimal evaluation (tie-breaker and independent pin).
+# ---------------------------------------------------------------------------------
+
+def dec_f(func: str, x: float, digits: int = 60) -> decimal.Decimal:
+    """f(x) for a double x, to about ``digits`` significant digits, in decimal."""
+    ctx = decimal.Context(prec=digits + 40, Emax=999999, Emin=-999999)
+    d = decimal.Decimal(x)  # exact value of the double
+    if func == "texp":
+        return ctx.exp(d)
+    if func == "texpm1":
+        if abs(x) < 1e-3:  # series with exact terms, avoids 1 - 1 cancellation
+            term, s, k = d, d, 1
+            while True:
+                k += 1
+                term = ctx.divide(ctx.multiply(term, d), k)
+                if term == 0 or abs(term) < abs(s) * decimal.Decimal(10) ** -(digits + 20):
+                    return s
+                s = ctx.add(s, term)
+        return ctx.subtract(ctx.exp(d), 1)
+    if func == "tlog":
+        return ctx.ln(d)
+    if func == "tlog1p":
+        return ctx.ln(ctx.add(d, 1))  # 1 + x is exact at this precision
+    raise KeyError(func)
+
+
+def round_to_double(v: decimal.Decimal) -> float:
+    """Nearest double (ties to even) of a decimal value; Python's float() of a
+    decimal string is correctly rounded, including subnormals and overflow."""
+    try:
+        return float(v)
+    except OverflowError:
+        return float("inf") if v > 0 else float("-inf")

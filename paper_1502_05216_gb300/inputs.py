@@ -1,0 +1,125 @@
+"""Seeded synthetic inputs for the twofold exp/log workloads.
+
+This module holds no arithmetic of the twofold method: it only draws argument
+arrays.  Both the CUDA path's tests and benchmark and the CPU oracle's tests
+take their inputs from here, so the two sides always see identical bits.
+
+Every element is a pure function of (seed, stream, index): a counter-based
+generator, SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014), applied to the counter
+    c = seed * 2**40 + stream * 2**36 + i
+as the (c+1)-th output of a SplitMix64 sequence started at state 0, i.e.
+    z = (c + 1) * 0x9E3779B97F4A7C15  (mod 2**64)
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EB
+    z =  z ^ (z >> 31).
+A uniform U in [0, 1) is (z >> 11) * 2**-53.  Any single element can therefore
+be regenerated on its own, which is how sampled oracle checks at full size work.
+
+A twofold argument is the pair x0 + x1 with x1 = RN(x0 * u * 2**-p), u uniform
+in [-1, 1] and p = 53 (double) or 24 (float): a perturbation of at most one ulp
+scale, as produced by a preceding twofold operation (paper, "Overview").
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# stream ids (each draw of an element uses its own stream)
+S_MAG, S_SIGN, S_PERT, S_PICK, S_AUX = 0, 1, 2, 3, 4
+
+
+def splitmix64(counter: np.ndarray) -> np.ndarray:
+    """SplitMix64 output for each uint64 counter (wrapping arithmetic)."""
+    with np.errstate(over="ignore"):
+        z = (counter.astype(np.uint64) + np.uint64(1)) * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed: int, stream: int, n: int, start: int = 0) -> np.ndarray:
+    """U in [0, 1) with 53 random bits, elements start .. start+n-1."""
+    if not (0 <= seed < 2**24 and 0 <= stream < 16 and 0 <= start and start + n <= 2**36):
+        raise ValueError("seed/stream/index out of the generator's counter layout")
+    base = (seed << 40) | (stream << 36)
+    c = np.arange(start, start + n, dtype=np.uint64) + np.uint64(base)
+    return (splitmix64(c) >> np.uint64(11)).astype(np.float64) * 2.0**-53
+
+
+def _perturb(x0: np.ndarray, seed: int, n: int, start: int, p: int) -> np.ndarray:
+    u = 2.0 * uniform(seed, S_PERT, n, start) - 1.0
+    with np.errstate(invalid="ignore", over="ignore"):
+        return x0 * u * 2.0**-p  # each product is exact up to the final rounding
+
+
+def _signs(seed: int, n: int, start: int) -> np.ndarray:
+    return np.where(uniform(seed, S_SIGN, n, start) < 0.5, -1.0, 1.0)
+
+
+def _loguniform(lo_exp: float, hi_exp: float, seed: int, n: int, start: int) -> np.ndarray:
+    return np.exp2(lo_exp + (hi_exp - lo_exp) * uniform(seed, S_MAG, n, start))
+
+
+# ---------------------------------------------------------------------------------
+# Workloads.  Each returns (x0, x1) as float64 (or float32 for dtype="f32").
+# ---------------------------------------------------------------------------------
+
+def texp_uniform(n: int, seed: int = 0, start: int = 0):
+    """texp over double, x0 uniform in [-708, 709] (1417 wide), x1 = x0*u*2^-53."""
+    x0 = -708.0 + 1417.0 * uniform(seed, S_MAG, n, start)
+    return x0, _perturb(x0, seed, n, start, 53)
+
+
+def exp_args(n: int, seed: int, start: int = 0):
+    """texp/texpm1: random sign, |x0| log-uniform in [2^-40, 708]."""
+    x0 = _signs(seed, n, start) * _loguniform(-40.0, math.log2(708.0), seed, n, start)
+    return x0, _perturb(x0, seed, n, start, 53)
+
+
+def log_args(n: int, seed: int, start: int = 0):
+    """tlog: x0 log-uniform in [2^-1020, 2^1020]."""
+    x0 = _loguniform(-1020.0, 1020.0, seed, n, start)
+    return x0, _perturb(x0, seed, n, start, 53)
+
+
+def log1p_args(n: int, seed: int, start: int = 0):
+    """tlog1p: half of the elements random sign with |x0| log-uniform in
+    [2^-40, 2^-10); the other half x0 = RN(t - 1) with t log-uniform in
+    [2^-30, 2^100], which spans -1 + 2^-30 .. 2^100."""
+    pick = uniform(seed, S_PICK, n, start) < 0.5
+    small = _signs(seed, n, start) * _loguniform(-40.0, -10.0, seed, n, start)
+    t = _loguniform(-30.0, 100.0, seed, n, start)
+    x0 = np.where(pick, small, t - 1.0)
+    return x0, _perturb(x0, seed, n, start, 53)
+
+
+def arith_args(n: int, seed: int, start: int = 0):
+    """tadd/tmul operands: random sign, |x0| log-uniform in [2^-20, 2^20]."""
+    x0 = _signs(seed, n, start) * _loguniform(-20.0, 20.0, seed, n, start)
+    return x0, _perturb(x0, seed, n, start, 53)
+
+
+# The double-precision workload of each function: generator and its seed.
+WORKLOADS = {
+    "texp": (exp_args, 2),
+    "texpm1": (exp_args, 3),
+    "tlog": (log_args, 4),
+    "tlog1p": (log1p_args, 5),
+    "tadd": (arith_args, 6),   # second operand: seed 7
+    "tmul": (arith_args, 8),   # second operand: seed 9
+}
+
+
+def workload(func: str, n: int, start: int = 0):
+    """(x0, x1[, y0, y1]) of the named function's n-element workload."""
+    gen, seed = WORKLOADS[func]
+    x = gen(n, seed, start)
+    if func in ("tadd", "tmul"):
+        return x + gen(n, seed + 1, start)
+    return x

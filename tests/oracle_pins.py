@@ -1,0 +1,314 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each ``pin_*`` function runs one family of checks against an oracle library
+handle and returns a list of failure strings (empty = pinned).  They are used
+twice: ``test_oracle.py`` asserts that the real oracle passes all of them, and
+``test_oracle_planted.py`` builds oracles with planted mistakes and asserts
+that each is caught by at least one pin.
+
+What the oracle is pinned to:
+  * Python's ``decimal`` module at 60+ significant digits (an independent
+    arbitrary-precision exp/ln) for the main part Z0 and the full value F;
+  * exact rational arithmetic (``fractions``) for tadd/tmul and for the
+    Taylor series of expm1/log1p near 0;
+  * closed forms: exp(0) = 1, expm1(+-0) = +-0, log(1) = 0, log1p(+-0) = +-0,
+    exp(twofold k ln 2) = 2^k, log(2^k) = k ln 2 (ln 2 from tests/golden);
+  * invariants: monotonicity of Z0, exp(x) exp(-x) = 1, Z0 independent of x1,
+    log(exp(x)) = x, log1p(y) = log(1 + y) when 1 + y is exact;
+  * the special-value rules (NaN, infinities, overflow/underflow).
+"""
+from __future__ import annotations
+
+import decimal
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+
+import oracle
+from paper_1502_05216_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+UNARY = ("texp", "texpm1", "tlog", "tlog1p")
+
+
+def _hiprec(fn):
+    """Run a pin with a 120-digit decimal context, so that plain operators on
+    Decimals (not only the explicit context calls) keep full precision."""
+    import functools
+
+    @functools.wraps(fn)
+    def run(*a, **k):
+        with decimal.localcontext(decimal.Context(prec=120, Emax=999999, Emin=-999999)):
+            return fn(*a, **k)
+    return run
+
+
+def golden_constants():
+    out = {}
+    with open(os.path.join(GOLDEN, "constants.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                out[k] = decimal.Decimal(v)
+    return out
+
+
+def _ctx(digits=60):
+    return decimal.Context(prec=digits + 40, Emax=999999, Emin=-999999)
+
+
+def dec_eval(func: str, d: decimal.Decimal, digits=60) -> decimal.Decimal:
+    """f(d) in decimal for an exact decimal argument d (independent of the oracle)."""
+    c = _ctx(digits)
+    if func == "texp":
+        return c.exp(d)
+    if func == "texpm1":
+        if abs(d) < decimal.Decimal("1e-3"):
+            term, s, k = d, d, 1
+            while True:
+                k += 1
+                term = c.divide(c.multiply(term, d), k)
+                if term == 0 or abs(term) < abs(s) * decimal.Decimal(10) ** -(digits + 20):
+                    return s
+                s = c.add(s, term)
+        return c.subtract(c.exp(d), 1)
+    if func == "tlog":
+        return c.ln(d)
+    if func == "tlog1p":
+        return c.ln(c.add(d, 1))
+    raise KeyError(func)
+
+
+def _D(x):
+    return decimal.Decimal(float(x))
+
+
+def _u(seed, n, stream=0):
+    return I.uniform(seed, stream, n)
+
+
+def mainpart_points():
+    """Argument sets per function: the workloads plus the awkward ranges."""
+    n = 150
+    pts = {}
+    x = [I.exp_args(n, 100)[0], I.texp_uniform(n, 101)[0],
+         -745.13 + (745.13 - 708.40) * _u(102, 60),          # subnormal results
+         709.70 + 0.0827 * _u(103, 30), np.array([1.0, -1.0, 0.5, 1e-300, -1e-300])]
+    pts["texp"] = np.concatenate(x)
+    x = [I.exp_args(n, 110)[0], -40.0 + 39.0 * _u(111, 40),
+         np.exp2(-60 + 40 * _u(112, 40)) * np.where(_u(113, 40) < 0.5, -1, 1), np.array([1.0, -1.0])]
+    pts["texpm1"] = np.concatenate(x)
+    x = [I.log_args(n, 120)[0], 1.0 + np.exp2(-52 + 50 * _u(121, 40)) * np.where(_u(122, 40) < 0.5, -1, 1),
+         np.exp2(-1074 + 52 * _u(123, 30)), np.array([2.0, 0.5, 10.0, 5e-324, 1.7976931348623157e308])]
+    pts["tlog"] = np.concatenate(x)
+    x = [I.log1p_args(n, 130)[0], -1.0 + np.exp2(-52 + 51 * _u(131, 40)),
+         np.exp2(-60 + 40 * _u(132, 40)) * np.where(_u(133, 40) < 0.5, -1, 1), np.array([1.0, -0.5, 1e300])]
+    pts["tlog1p"] = np.concatenate(x)
+    return pts
+
+
+@_hiprec
+def pin_mainpart_decimal(lib):
+    """Z0 equals the decimal value rounded to the nearest double."""
+    fails = []
+    for func, x0 in mainpart_points().items():
+        r = oracle.evaluate(func, x0, None, lib=lib)
+        for i, x in enumerate(x0):
+            want = oracle.round_to_double(dec_eval(func, _D(x)))
+            if not (r.Z0[i] == want or (math.isnan(want) and math.isnan(r.Z0[i]))):
+                fails.append(f"{func}({x!r}): Z0={r.Z0[i]!r} decimal={want!r}")
+    return fails
+
+
+def _close(G_h, G_l, G_dec, F_dec, rel=decimal.Decimal(2) ** -104):
+    c = _ctx(80)
+    diff = abs(c.subtract(c.add(_D(G_h), _D(G_l)), G_dec))
+    return diff <= rel * abs(F_dec) + decimal.Decimal(2) ** -1074
+
+
+@_hiprec
+def pin_deviation_decimal(lib):
+    """Gh + Gl equals F - Z0 with F = f(x0 + x1) evaluated in decimal from the
+    exact sum x0 + x1 (coupled and loosely coupled x1)."""
+    fails = []
+    pts = mainpart_points()
+    for func in UNARY:
+        x0 = pts[func]
+        # skip arguments whose result is not a finite nonzero value
+        for scale, seed in ((2.0**-53, 140), (2.0**-30, 141)):
+            x1 = x0 * (2 * _u(seed, x0.shape[0]) - 1) * scale
+            r = oracle.evaluate(func, x0, x1, lib=lib)
+            c = _ctx(80)
+            for i in range(x0.shape[0]):
+                if r.flags[i] & oracle.FL_EXACT:
+                    continue
+                d = c.add(_D(x0[i]), _D(x1[i]))
+                if func == "tlog" and d <= 0 or func == "tlog1p" and d <= -1:
+                    continue
+                F = dec_eval(func, d, 70)
+                G = c.subtract(F, _D(r.Z0[i]))
+                if not _close(r.Gh[i], r.Gl[i], G, F):
+                    fails.append(f"{func}({x0[i]!r}+{x1[i]!r}): G={r.Gh[i]!r}+{r.Gl[i]!r} decimal={G:.6e}")
+    return fails
+
+
+@_hiprec
+def pin_closed_forms(lib):
+    fails = []
+    ln2 = golden_constants()["ln2"]
+    c = _ctx(80)
+    # exp(0) = 1 and expm1(+-0) = +-0, log(1) = 0, log1p(+-0) = +-0, z1 = 0
+    for func, x, want in (("texp", 0.0, 1.0), ("texpm1", 0.0, 0.0), ("texpm1", -0.0, -0.0),
+                          ("tlog", 1.0, 0.0), ("tlog1p", 0.0, 0.0), ("tlog1p", -0.0, -0.0)):
+        r = oracle.evaluate(func, np.array([x]), np.array([0.0]), lib=lib)
+        if not (r.Z0[0] == want and math.copysign(1, r.Z0[0]) == math.copysign(1, want)
+                and r.Gh[0] == 0 and r.Gl[0] == 0):
+            fails.append(f"{func}({x}) = {r.Z0[0]!r} + {r.Gh[0]!r}, want {want!r} + 0")
+    # exp of the twofold k*ln2 is 2^k to 2^-100; log(2^k) is k*ln2 to 2^-100
+    ks = np.arange(-1000, 1001, 7)
+    x0 = np.array([float(k * ln2) for k in ks])
+    x1 = np.array([float(c.subtract(k * ln2, _D(a))) for k, a in zip(ks, x0)])
+    r = oracle.evaluate("texp", x0, x1, lib=lib)
+    for i, k in enumerate(ks):
+        v = c.add(c.add(_D(r.Z0[i]), _D(r.Gh[i])), _D(r.Gl[i]))
+        delta = _D(x0[i]) + _D(x1[i]) - k * ln2   # |delta| <= 2^-97: e^delta = 1 + delta + O(2^-195)
+        want = c.power(2, int(k)) * (1 + delta)
+        if abs(v - want) > want * decimal.Decimal(2) ** -100 + decimal.Decimal(2) ** -1073:
+            fails.append(f"texp({k} ln2) = {v:.30e}, want 2^{k}")
+    ks = np.arange(-1074, 1024, 5)
+    y0 = np.array([math.ldexp(1.0, int(k)) for k in ks])
+    r = oracle.evaluate("tlog", y0, np.zeros_like(y0), lib=lib)
+    for i, k in enumerate(ks):
+        v = c.add(c.add(_D(r.Z0[i]), _D(r.Gh[i])), _D(r.Gl[i]))
+        want = k * ln2
+        if abs(v - want) > abs(want) * decimal.Decimal(2) ** -100:
+            fails.append(f"tlog(2^{k}) = {v:.30e}, want {want:.30e}")
+    return fails
+
+
+def _series(func, x: Fraction, terms=7):
+    s, p = Fraction(0), Fraction(1)
+    for j in range(1, terms + 1):
+        p = p * x
+        if func == "texpm1":
+            s += p / math.factorial(j)
+        else:
+            s += (-1) ** (j + 1) * p / j
+    return s
+
+
+@_hiprec
+def pin_series(lib):
+    """expm1 and log1p near 0 against their Taylor series in exact rationals."""
+    fails = []
+    x0 = np.exp2(-90 + 70 * _u(150, 200)) * np.where(_u(151, 200) < 0.5, -1, 1)
+    for func in ("texpm1", "tlog1p"):
+        r = oracle.evaluate(func, x0, np.zeros_like(x0), lib=lib)
+        for i, x in enumerate(x0):
+            S = _series(func, Fraction(float(x)))
+            if float(S) != r.Z0[i]:
+                fails.append(f"{func}({x!r}) Z0={r.Z0[i]!r} series={float(S)!r}")
+            got = Fraction(float(r.Z0[i])) + Fraction(float(r.Gh[i])) + Fraction(float(r.Gl[i]))
+            if abs(got - S) > abs(S) * Fraction(1, 2**104):
+                fails.append(f"{func}({x!r}) Z0+G off the series by {float(abs(got - S) / abs(S)):.3e}")
+    return fails
+
+
+@_hiprec
+def pin_invariants(lib):
+    fails = []
+    # Z0 monotone in x0
+    for func, gen in (("texp", I.exp_args), ("texpm1", I.exp_args), ("tlog", I.log_args),
+                      ("tlog1p", I.log1p_args)):
+        x0 = np.sort(gen(4000, 160)[0])
+        r = oracle.evaluate(func, x0, None, lib=lib)
+        if np.any(np.diff(r.Z0) < 0):
+            fails.append(f"{func}: Z0 not monotone")
+    # main part independent of x1
+    x0, x1 = I.exp_args(2000, 161)
+    for func in ("texp", "texpm1"):
+        a = oracle.evaluate(func, x0, None, lib=lib)
+        b = oracle.evaluate(func, x0, x1 * 2.0**20, lib=lib)
+        if not np.array_equal(a.Z0, b.Z0):
+            fails.append(f"{func}: Z0 depends on x1")
+    # exp(x) exp(-x) = 1
+    x0 = (2 * _u(162, 300) - 1) * 600  # e^-x stays well above the subnormal range
+    p = oracle.evaluate("texp", x0, None, lib=lib)
+    m = oracle.evaluate("texp", -x0, None, lib=lib)
+    for i in range(x0.shape[0]):
+        a = Fraction(float(p.Z0[i])) + Fraction(float(p.Gh[i])) + Fraction(float(p.Gl[i]))
+        b = Fraction(float(m.Z0[i])) + Fraction(float(m.Gh[i])) + Fraction(float(m.Gl[i]))
+        if abs(a * b - 1) > Fraction(1, 2**102):
+            fails.append(f"texp({x0[i]!r}) * texp(-x) - 1 = {float(a * b - 1):.3e}")
+    # log(exp(x)) = x, with exp(x) as the twofold (Z0, Gh)
+    x0 = np.exp2(-4 + 13 * _u(163, 300)) * np.where(_u(164, 300) < 0.5, -1, 1)
+    e = oracle.evaluate("texp", x0, None, lib=lib)
+    l = oracle.evaluate("tlog", e.Z0, e.Gh, lib=lib)
+    for i in range(x0.shape[0]):
+        v = Fraction(float(l.Z0[i])) + Fraction(float(l.Gh[i])) + Fraction(float(l.Gl[i]))
+        if abs(v - Fraction(float(x0[i]))) > abs(Fraction(float(x0[i]))) * Fraction(1, 2**100):
+            fails.append(f"tlog(texp({x0[i]!r})) = {float(v)!r}")
+    # log1p(y) = log(1 + y) when 1 + y is exact
+    y = np.ldexp(np.floor(_u(165, 300) * 2**20), -18) - 0.5  # multiples of 2^-18 in [-0.5, 3.5)
+    a = oracle.evaluate("tlog1p", y, None, lib=lib)
+    b = oracle.evaluate("tlog", 1.0 + y, None, lib=lib)
+    if not np.array_equal(a.Z0, b.Z0):
+        fails.append("tlog1p(y) main part != tlog(1 + y) main part")
+    d = np.abs((a.Gh - b.Gh) + (a.Gl - b.Gl))
+    if np.any(d > np.abs(a.Z0) * 2.0**-104):
+        fails.append("tlog1p(y) deviation != tlog(1 + y) deviation")
+    return fails
+
+
+@_hiprec
+def pin_special(lib):
+    """The special-value rules (NaN, infinities, overflow, underflow, domain)."""
+    inf, nan = math.inf, math.nan
+    cases = [  # func, x0, x1, Z0, z1
+        ("texp", nan, 0.0, nan, nan), ("texp", 1.0, nan, math.e, nan),
+        ("texp", inf, 0.0, inf, 0.0), ("texp", -inf, 0.0, 0.0, 0.0),
+        ("texp", 710.0, 1e-300, inf, 0.0), ("texp", -746.0, 0.0, 0.0, 0.0),
+        ("texp", 1.0, inf, math.e, inf),
+        ("texpm1", -inf, 0.0, -1.0, 0.0), ("texpm1", inf, 0.0, inf, 0.0),
+        ("texpm1", 710.0, 0.0, inf, 0.0), ("texpm1", nan, 0.0, nan, nan),
+        ("tlog", -1.0, 0.0, nan, nan), ("tlog", 0.0, 0.0, -inf, 0.0), ("tlog", -0.0, 0.0, -inf, 0.0),
+        ("tlog", inf, 0.0, inf, 0.0), ("tlog", 1.0, nan, 0.0, nan), ("tlog", nan, 0.0, nan, nan),
+        ("tlog", 1.0, -2.0, 0.0, nan), ("tlog", 1.0, -1.0, 0.0, -inf), ("tlog", 2.0, inf, math.log(2), inf),
+        ("tlog1p", -1.0, 0.0, -inf, 0.0), ("tlog1p", -2.0, 0.0, nan, nan), ("tlog1p", inf, 0.0, inf, 0.0),
+        ("tlog1p", 0.0, -1.0, 0.0, -inf), ("tlog1p", 0.0, -3.0, 0.0, nan),
+    ]
+    fails = []
+    for func, x0, x1, Z0, z1 in cases:
+        r = oracle.evaluate(func, np.array([x0]), np.array([x1]), lib=lib)
+        okz = (r.Z0[0] == Z0) or (math.isnan(Z0) and math.isnan(r.Z0[0]))
+        okg = bool(r.flags[0] & oracle.FL_EXACT) and ((r.Gh[0] == z1) or (math.isnan(z1) and math.isnan(r.Gh[0])))
+        if not (okz and okg):
+            fails.append(f"{func}({x0}, {x1}) = ({r.Z0[0]}, {r.Gh[0]}, flags {r.flags[0]}), want ({Z0}, {z1})")
+    return fails
+
+
+@_hiprec
+def pin_arith(lib):
+    """tadd/tmul: Z0 is the plain double op; Gh + Gl is the exact deviation."""
+    fails = []
+    x0, x1, y0, y1 = I.workload("tadd", 400, 0)
+    for func, op in (("tadd", lambda a, b: a + b), ("tmul", lambda a, b: a * b)):
+        r = oracle.evaluate(func, x0, x1, y0, y1, lib=lib)
+        if not np.array_equal(r.Z0, op(x0, y0)):
+            fails.append(f"{func}: Z0 is not the plain double op")
+        for i in range(x0.shape[0]):
+            X = Fraction(float(x0[i])) + Fraction(float(x1[i]))
+            Y = Fraction(float(y0[i])) + Fraction(float(y1[i]))
+            F = op(X, Y)
+            G = F - Fraction(float(r.Z0[i]))
+            got = Fraction(float(r.Gh[i])) + Fraction(float(r.Gl[i]))
+            scale = abs(F) if func == "tmul" else abs(X) + abs(Y)
+            if abs(got - G) > scale * Fraction(1, 2**104):
+                fails.append(f"{func}[{i}]: G={float(got)!r}, exact {float(G)!r}")
+    return fails
+
+
+ALL_PINS = [pin_mainpart_decimal, pin_deviation_decimal, pin_closed_forms, pin_series,
+            pin_invariants, pin_special, pin_arith]

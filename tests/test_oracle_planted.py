@@ -1,0 +1,23 @@
+"""Each planted mistake in the oracle (a dropped term, a wrong sign, a wrong
+base, a transposed operand, a wrong rounding) must be caught by some pin."""
+import pytest
+
+import oracle
+import oracle_pins as P
+
+PLANTS = {1: "texp drops the x1 term", 2: "tlog correction has the wrong sign",
+          3: "tlog1p correction uses the wrong base", 4: "main part rounded toward zero",
+          5: "tmul drops a cross term", 6: "tadd error term with transposed operands",
+          7: "texp rounds x0 + x1 to double first"}
+
+
+@pytest.mark.parametrize("k", sorted(PLANTS), ids=lambda k: PLANTS[k].replace(" ", "_"))
+def test_planted_mistake_is_caught(k):
+    path = oracle.build(force=True, defines=(f"TFO_PLANT={k}",), name=f"libtforacle_plant{k}.so")
+    lib = oracle.load(path)
+    caught = []
+    for pin in P.ALL_PINS:
+        if pin(lib):
+            caught.append(pin.__name__)
+            break
+    assert caught, f"planted mistake {k} ({PLANTS[k]}) passed every pin"
