@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput of the double-twofold exp/log kernels on one GB300 (or N, weak scaling).
+
+One step = one pass of the whole path over its synthetic batch: texp, texpm1,
+tlog, tlog1p, tadd and tmul, each over n = 2^26 double twofolds (SoA x0, x1 ->
+z0, z1; 1 GiB in + 1 GiB out per unary function), every input resident in HBM
+before the timed region.  Inputs are 512 MiB per array, larger than L2, so no
+flush is needed between iterations.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is elements processed per second by
+all ranks (Gelem/s); ``e2e`` is the same metric through the host-array API
+(pinned host -> device -> host, copies inside the timed region); ``roofline``
+is for the kernel with the longest average launch; ``cpu_baseline`` is the
+CPU oracle timed on this host's cores on a bounded sample.
+
+``--impl reference`` times the CPU oracle (binary128, all host cores) as the
+reference arm on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FUNCS = ("texp", "texpm1", "tlog", "tlog1p", "tadd", "tmul")
+METRIC = "double-twofold texp/tlog Gelem/s at n=2^26 and % of FP64/HBM roofline"
+WORKLOAD = ("texp, texpm1, tlog, tlog1p (+ tadd, tmul) over double twofolds, n=2^26 each: exp/expm1 "
+            "args random sign |x0| log-uniform in [2^-40, 708]; log x0 log-uniform in [2^-1020, 2^1020]; "
+            "log1p half |x0| log-uniform in [2^-40, 2^-10), half -1+2^-30 .. 2^100; x1 = x0*u*2^-53")
+
+# FP64 pipe instructions (DADD + DMUL + DFMA, thread level) per element of each
+# kernel on its workload: the algorithmic work of the FP64-bound kernels.  Counted
+# with ncu (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum / n).
+FP64_PER_ELEM = {"texp": 71.0, "texpm1": 78.0, "tlog": 130.0, "tlog1p": 135.0, "tadd": 5.0, "tmul": 5.0}
+FP64_COUNT_SOURCE = "source count (not yet checked with ncu)"
+# HBM bytes per element: SoA doubles in + out.
+BYTES_PER_ELEM = {"texp": 32, "texpm1": 32, "tlog": 32, "tlog1p": 32, "tadd": 48, "tmul": 48}
+# DRAM traffic per launch from one ncu capture (dram__bytes_read.sum + write.sum),
+# None when no capture of the current kernels exists.
+TRAFFIC_PER_LAUNCH = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--log2n", type=int, default=26)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--funcs", default=",".join(FUNCS),
+                    help="comma-separated subset (for profiling a single kernel)")
+    return ap.parse_args()
+
+
+def dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if gpu_id:
+                cmd += ["-i", gpu_id]
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.6)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.p.terminate()
+        self.p.wait(timeout=10)
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ("active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 10:
+                continue
+            try:
+                sm.append(float(c[2]))
+                mx.append(float(c[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], c[6:10]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------------
+
+def oracle_rate(budget_s: float, per_func_cap: int = 1 << 22):
+    """Time the CPU oracle on a bounded sample of every function's workload:
+    elements/s over all host threads, plus the sample description."""
+    import oracle
+    from paper_1502_05216_gb300 import inputs as I
+    lib = oracle.load()
+    probe = 1 << 13
+    t0 = time.perf_counter()
+    for f in FUNCS:
+        oracle.evaluate(f, *I.workload(f, probe), lib=lib)
+    rate0 = len(FUNCS) * probe / (time.perf_counter() - t0)
+    m = int(min(per_func_cap, max(probe, budget_s * rate0 / len(FUNCS))))
+    args = {f: I.workload(f, m, start=1 << 30) for f in FUNCS}
+    t0 = time.perf_counter()
+    for f in FUNCS:
+        oracle.evaluate(f, *args[f], lib=lib)
+    dt = time.perf_counter() - t0
+    sample = f"{m} elements of each of the 6 functions' workloads (indices from 2^30), {dt:.1f} s"
+    return len(FUNCS) * m / dt, oracle.threads(), sample, m, dt
+
+
+def reference_arm(a, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1502_05216_gb300 import inputs as I
+    lib = oracle.load()
+    budget = max(1.0, min(8.0, 150.0 / (a.steps + a.warmup)))
+    _, cores, _, m, _ = oracle_rate(budget * 0.5)
+    args = {f: I.workload(f, m, start=1 << 31) for f in FUNCS}
+    for _ in range(a.warmup):
+        for f in FUNCS:
+            oracle.evaluate(f, *args[f], lib=lib)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        for f in FUNCS:
+            oracle.evaluate(f, *args[f], lib=lib)
+    dt = (time.perf_counter() - t0) / a.steps
+    v = len(FUNCS) * m / dt / 1e9
+    sample = f"each step: {m} elements of each of the 6 functions' workloads (bounded sample of n=2^26)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "Gelem/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f128", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": 1 << a.log2n, "functions": list(FUNCS)},
+        "cpu_baseline": {"value": v, "unit": "Gelem/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------
+
+def fp64_peak(dev):
+    """Measured FP64 pipe rate (DFMA thread-instructions/s) of this GPU, from the
+    calibration kernel; best of 5."""
+    import ctypes
+    import torch
+    from paper_1502_05216_gb300 import build
+    lib = ctypes.CDLL(build.PROBE_LIB)
+    lib.tfp_dfma.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads, iters = sms * 8, 256, 6000
+    out = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    best = 0.0
+    for i in range(7):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        rc = lib.tfp_dfma(out.data_ptr(), blocks, threads, iters, st.cuda_stream)
+        e1.record(st)
+        e1.synchronize()
+        if rc != 0:
+            raise RuntimeError(f"tfp_dfma failed ({rc})")
+        if i >= 2:
+            best = max(best, blocks * threads * iters * 8 / (e0.elapsed_time(e1) * 1e-3))
+    return best, sms
+
+
+def ours(a, world, rank, local):
+    global FUNCS
+    FUNCS = tuple(f for f in a.funcs.split(",") if f)
+    import torch
+    from paper_1502_05216_gb300 import build, inputs as I, tf
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build()
+    tf.load()
+    n = 1 << a.log2n
+    start = rank * n  # weak scaling: each rank evaluates its own n elements
+
+    host = {f: I.workload(f, n, start=start) for f in FUNCS}
+    dargs = {f: [torch.from_numpy(x).to(dev) for x in host[f]] for f in FUNCS}
+    z0 = torch.empty(n, dtype=torch.float64, device=dev)
+    z1 = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step(evs=None):
+        for f in FUNCS:
+            if evs is not None:
+                evs[f][0].record(st)
+            tf.FUNCS[f](*dargs[f], out=(z0, z1), stream=st)
+            if evs is not None:
+                evs[f][1].record(st)
+
+    peak, sms = fp64_peak(dev)
+    for _ in range(a.warmup):
+        step()
+    evs = [{f: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for f in FUNCS}
+           for _ in range(a.steps)]
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    clocks = Clocks(gpu_id)
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    for k in range(a.steps):
+        step(evs[k])
+    t1.record(st)
+    barrier()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1) / a.steps
+    kern_ms = {f: statistics.mean(e[f][0].elapsed_time(e[f][1]) for e in evs) for f in FUNCS}
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    elems = world * n * len(FUNCS)
+    value = elems / (ms * 1e-3) / 1e9
+
+    # end to end through the host-array API (pinned host buffers, copies inside)
+    e2e = None
+    if not a.no_e2e:
+        pin = {f: [torch.from_numpy(x).pin_memory() for x in host[f]] for f in FUNCS}
+        out = (torch.empty(n, dtype=torch.float64, pin_memory=True),
+               torch.empty(n, dtype=torch.float64, pin_memory=True))
+        pipe = tf.HostPipeline(dev)
+        for f in FUNCS:
+            pipe.run(f, *pin[f], out=out)
+        ke = max(2, a.steps // 4)
+        barrier()
+        c0 = time.perf_counter()
+        for _ in range(ke):
+            for f in FUNCS:
+                pipe.run(f, *pin[f], out=out)
+        barrier()
+        dt = (time.perf_counter() - c0) / ke
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = sum(8 * n * len(host[f]) for f in FUNCS)
+        e2e = {"value": elems / dt / 1e9, "unit": "Gelem/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 16 * n * len(FUNCS), "ms_per_step": dt * 1e3,
+               "pipeline": {"chunk": pipe.chunk, "streams": pipe.depth}}
+
+    if rank != 0:
+        return
+    dom = max(FUNCS, key=lambda f: kern_ms[f])
+    d = kern_ms[dom] * 1e-3
+    achieved = FP64_PER_ELEM[dom] * n / d / 1e9
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak / 1e9,
+            "unit": "FP64 Ginst/s", "frac": achieved / (peak / 1e9),
+            "peak_source": f"measured: DFMA calibration kernel on this GPU ({sms} SMs)",
+            "fp64_inst_per_elem": FP64_PER_ELEM[dom], "fp64_count_source": FP64_COUNT_SOURCE,
+            "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+            "hbm_view": {"achieved_gbs": BYTES_PER_ELEM[dom] * n / d / 1e9, "peak_gbs": 6804.4,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}
+    per = {f: {"ms": kern_ms[f], "gelem_s": n / (kern_ms[f] * 1e-3) / 1e9,
+               "fp64_frac": FP64_PER_ELEM[f] * n / (kern_ms[f] * 1e-3) / peak,
+               "hbm_gbs": BYTES_PER_ELEM[f] * n / (kern_ms[f] * 1e-3) / 1e9} for f in FUNCS}
+    cpu = None
+    if world == 1 and not a.no_cpu_baseline:
+        rate, cores, sample, _, _ = oracle_rate(12.0)
+        cpu = {"value": rate / 1e9, "unit": "Gelem/s", "cores": cores, "kind": "oracle", "sample": sample}
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "functions": list(FUNCS),
+                   "l2": "no flush: every input array (512 MiB) is larger than L2", "parallelism": f"dp{world}"},
+        "roofline": roof, "per_func": per, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": len(FUNCS) * a.steps, "clocks": ck,
+    }), flush=True)
+
+
+def main():
+    a = parse()
+    world, rank, local = dist()
+    if world != a.gpus and not (world == 1 and a.gpus == 1):
+        if rank == 0:
+            print(f"--gpus {a.gpus} but WORLD_SIZE={world}: launch with torchrun for N > 1", file=sys.stderr)
+        if world == 1:
+            sys.exit(2)
+    if a.impl == "reference":
+        reference_arm(a, world, rank)
+    else:
+        ours(a, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

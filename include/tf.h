@@ -1,0 +1,108 @@
+/*
+ * tf.h -- C ABI of the GB300 twofold exp/log library (libtf.so).
+ *
+ * A twofold is a pair of floating-point numbers x0 + x1: the main part x0 is an
+ * ordinary double and x1 assesses its deviation from the exact value (paper,
+ * "Overview").  A twofold function z0 + z1 = f(x0 + x1) returns as main part z0
+ * the correctly rounded f(x0) -- it depends on x0 only -- and as z1 a 1x-precise
+ * estimate of the deviation f(x0 + x1) - z0, so that z0 + z1 is nearly
+ * 2x-precise (paper, "Twofold exponent" > "Method summary").
+ *
+ * Common contract of the array entry points below:
+ *   - Layout: structure of arrays.  Element i of the argument is x0[i] + x1[i];
+ *     element i of the result is z0[i] + z1[i].  All arrays are contiguous
+ *     doubles of length n.
+ *   - Ownership: every pointer is a DEVICE pointer owned by the caller; the
+ *     library allocates and frees nothing and keeps no pointer after the call.
+ *   - x1 (and y1 for the binary operations) may be NULL: the argument is then
+ *     "dotted", x1 = 0 (the paper's texp0/texpm10/tlog0/tlog1p0 variants).
+ *     x0, z0 and z1 must not be NULL when n > 0.
+ *   - Aliasing: z0 may be x0 and z1 may be x1 (in-place update); any other
+ *     overlap of an output with an input or with the other output is undefined.
+ *   - Alignment: pointers must be 8-byte aligned.  When every pointer is
+ *     16-byte aligned the kernels use 128-bit loads and stores; otherwise a
+ *     scalar kernel runs (same results, bit for bit).
+ *   - Stream: the work is enqueued on `stream` (a cudaStream_t passed as
+ *     void*, NULL = the legacy default stream) and the call returns without
+ *     waiting.  Errors of the execution itself surface at the caller's next
+ *     synchronisation with that stream.
+ *   - n == 0 is a no-op that returns TF_OK; n < 0 returns TF_ERR_SIZE.
+ *   - Return value: TF_OK or one of the TF_ERR_* codes; nothing is printed,
+ *     nothing is launched when an argument check fails.
+ *   - Numerics: all arithmetic is IEEE binary64, round to nearest even, no
+ *     flush of subnormals.  Special values: NaN in x0 gives z0 = z1 = NaN;
+ *     NaN in x1 with a numeric z0 gives z1 = NaN; when z0 is +-Inf, or 0 by
+ *     underflow, z1 = 0 (the paper's "avoid NaN" remark after the texp
+ *     algorithm and its "domain errors" remark after tlog).
+ */
+#ifndef TF_H
+#define TF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    TF_OK = 0,
+    TF_ERR_NULL = 1,     /* a required pointer is NULL */
+    TF_ERR_SIZE = 2,     /* n < 0, or n beyond the supported range */
+    TF_ERR_ALIGN = 3,    /* a pointer is not 8-byte aligned */
+    TF_ERR_LAUNCH = 4,   /* the kernel launch was rejected (cudaGetLastError) */
+    TF_ERR_NODEVICE = 5, /* no usable CUDA device */
+    TF_ERR_ARG = 6       /* another invalid argument (e.g. an unknown variant) */
+};
+
+/* Twofold exponent z0 + z1 = e^(x0 + x1).
+ * Paper: "Twofold exponent" > "Algorithm summary", algorithms texp and texp0
+ * (with pexp0 computed here by a k ln2 + j ln2/256 reduction, table and
+ * Taylor polynomial in twofold arithmetic).  z0 = RN(e^x0): +Inf for
+ * x0 >= 709.782712893384, subnormal below x0 = -708.396..., 0 at or below
+ * x0 = -745.1332191019412. */
+int tf_texp(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream);
+
+/* Twofold z0 + z1 = e^(x0 + x1) - 1.
+ * Paper: "Twofold exponent" > "Algorithm summary", texpm1 / texpm10 (with
+ * pexpm10).  z0 = RN(e^x0 - 1); z0 = -1 for x0 below about -37.43. */
+int tf_texpm1(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream);
+
+/* Twofold logarithm z0 + z1 = log(y0 + y1).
+ * Paper: "Twofold logarithm" > "Newton inversion" and "Algorithm summary"
+ * (tlog, plog, tlog0): one Newton step on e^x seeded by a 1x-precise log1p.
+ * z0 = RN(log y0); y0 < 0 or NaN gives NaN, y0 = +-0 gives -Inf (z1 = 0).
+ * y1 may be any double: a twofold that is not renormalised takes a slower
+ * path in its warp. */
+int tf_tlog(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
+
+/* Twofold z0 + z1 = log(1 + y0 + y1).
+ * Paper: "Twofold logarithm" > "Newton inversion" and "Algorithm summary"
+ * (tlog1p, plog1p, tlog1p0): Newton step on e^x - 1.  z0 = RN(log1p y0);
+ * y0 < -1 gives NaN, y0 = -1 gives -Inf (z1 = 0). */
+int tf_tlog1p(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
+
+/* Twofold sum z0 + z1 = (x0 + x1) + (y0 + y1).
+ * Paper: "Overview" (z0 = x0 (+) y0, the ordinary double sum) and
+ * "Twofolds update" > "Twofold bugs", Algorithm 2.2 (the exact rounding error
+ * of x0 (+) y0); z1 = that error + (x1 + y1).  z0 is NOT renormalised. */
+int tf_tadd(const double* x0, const double* x1, const double* y0, const double* y1,
+            double* z0, double* z1, int64_t n, void* stream);
+
+/* Twofold product z0 + z1 = (x0 + x1)(y0 + y1).
+ * Paper: "Overview" (z0 = x0 (*) y0) and "Twofold exponent" > "Method summary"
+ * (FMA-based exact product, 2 MUL + 1 FMA + 1 ADD per twofold-by-dotted step):
+ * z1 = fma(x0, y0, -z0) + (x0 y1 + x1 y0); the x1 y1 term is dropped. */
+int tf_tmul(const double* x0, const double* x1, const double* y0, const double* y1,
+            double* z0, double* z1, int64_t n, void* stream);
+
+/* Human-readable name of an error code (static storage, never NULL). */
+const char* tf_strerror(int code);
+
+/* Version of this ABI: (major << 16) | minor. */
+int tf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TF_H */

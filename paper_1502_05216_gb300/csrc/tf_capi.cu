@@ -1,0 +1,229 @@
+// tf_capi.cu -- elementwise twofold kernels for sm_103a and the C ABI of include/tf.h.
+//
+// One thread evaluates two consecutive elements (two independent chains of
+// FP64 work for the scheduler) and moves them with 128-bit loads and stores
+// when every pointer is 16-byte aligned.  All 32 lanes of a warp always run
+// the element code -- lanes past the end work on a harmless dummy argument and
+// store nothing -- so that the warp-uniform votes (__any_sync) that guard the
+// rare special-case paths see a full warp.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tf.h"
+#include "tf_core.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct OpExp {
+    static constexpr double dummy = 0.0;
+    __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp1(a, b, z0, z1); }
+};
+struct OpExpm1 {
+    static constexpr double dummy = 0.0;
+    __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texpm11(a, b, z0, z1); }
+};
+struct OpLog {
+    static constexpr double dummy = 1.0;
+    __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1(a, b, z0, z1); }
+};
+struct OpLog1p {
+    static constexpr double dummy = 0.0;
+    __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1p1(a, b, z0, z1); }
+};
+struct OpAdd {
+    __device__ static void eval(double a, double b, double c, double d, double& z0, double& z1) {
+        tf::tadd1(a, b, c, d, z0, z1);
+    }
+};
+struct OpMul {
+    __device__ static void eval(double a, double b, double c, double d, double& z0, double& z1) {
+        tf::tmul1(a, b, c, d, z0, z1);
+    }
+};
+
+__device__ __forceinline__ double2 ld2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
+__device__ __forceinline__ void st2(double* p, double a, double b) {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(a, b));  // streaming: outputs are not re-read
+}
+
+// Unary, 2 elements per thread, 128-bit I/O.  Thread t covers elements 2t, 2t+1.
+template <class Op>
+__global__ void __launch_bounds__(kThreads) unary_v2(const double* __restrict__ x0, const double* __restrict__ x1,
+                                                     double* z0, double* z1, int64_t n) {
+    int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    int64_t i = 2 * t;
+    double a0 = Op::dummy, a1 = Op::dummy, b0 = 0.0, b1 = 0.0;
+    bool full = i + 1 < n;
+    bool half = i + 1 == n;
+    if (full) {
+        double2 a = ld2(x0 + i);
+        a0 = a.x;
+        a1 = a.y;
+        if (x1) {
+            double2 b = ld2(x1 + i);
+            b0 = b.x;
+            b1 = b.y;
+        }
+    } else if (half) {
+        a0 = x0[i];
+        b0 = x1 ? x1[i] : 0.0;
+    }
+    double r0, r1, s0, s1;
+    Op::eval(a0, b0, r0, r1);
+    Op::eval(a1, b1, s0, s1);
+    if (full) {
+        st2(z0 + i, r0, s0);
+        st2(z1 + i, r1, s1);
+    } else if (half) {
+        z0[i] = r0;
+        z1[i] = r1;
+    }
+}
+
+// Unary, 1 element per thread, scalar I/O (pointers not 16-byte aligned).
+template <class Op>
+__global__ void __launch_bounds__(kThreads) unary_v1(const double* x0, const double* x1, double* z0, double* z1,
+                                                     int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    bool in = i < n;
+    double a = in ? x0[i] : Op::dummy;
+    double b = (in && x1) ? x1[i] : 0.0;
+    double r0, r1;
+    Op::eval(a, b, r0, r1);
+    if (in) {
+        z0[i] = r0;
+        z1[i] = r1;
+    }
+}
+
+template <class Op>
+__global__ void __launch_bounds__(kThreads) binary_v2(const double* __restrict__ x0, const double* __restrict__ x1,
+                                                      const double* __restrict__ y0, const double* __restrict__ y1,
+                                                      double* z0, double* z1, int64_t n) {
+    int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    int64_t i = 2 * t;
+    if (i + 1 < n) {
+        double2 a = ld2(x0 + i), c = ld2(y0 + i);
+        double2 b = x1 ? ld2(x1 + i) : make_double2(0.0, 0.0);
+        double2 d = y1 ? ld2(y1 + i) : make_double2(0.0, 0.0);
+        double r0, r1, s0, s1;
+        Op::eval(a.x, b.x, c.x, d.x, r0, r1);
+        Op::eval(a.y, b.y, c.y, d.y, s0, s1);
+        st2(z0 + i, r0, s0);
+        st2(z1 + i, r1, s1);
+    } else if (i < n) {
+        double r0, r1;
+        Op::eval(x0[i], x1 ? x1[i] : 0.0, y0[i], y1 ? y1[i] : 0.0, r0, r1);
+        z0[i] = r0;
+        z1[i] = r1;
+    }
+}
+
+template <class Op>
+__global__ void __launch_bounds__(kThreads) binary_v1(const double* x0, const double* x1, const double* y0,
+                                                      const double* y1, double* z0, double* z1, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < n) {
+        double r0, r1;
+        Op::eval(x0[i], x1 ? x1[i] : 0.0, y0[i], y1 ? y1[i] : 0.0, r0, r1);
+        z0[i] = r0;
+        z1[i] = r1;
+    }
+}
+
+inline bool al(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+// Largest n accepted (1 TiB per array): grids stay below 2^31 - 1 blocks.
+constexpr int64_t kMaxN = (int64_t)1 << 37;
+
+int launch_status() {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return TF_OK;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return TF_ERR_NODEVICE;
+    return TF_ERR_LAUNCH;
+}
+
+template <class Op>
+int run_unary(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream) {
+    if (n < 0 || n > kMaxN) return TF_ERR_SIZE;
+    if (n == 0) return TF_OK;
+    if (!x0 || !z0 || !z1) return TF_ERR_NULL;
+    if (!al(x0, 8) || !al(z0, 8) || !al(z1, 8) || (x1 && !al(x1, 8))) return TF_ERR_ALIGN;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bool vec = al(x0, 16) && al(z0, 16) && al(z1, 16) && (!x1 || al(x1, 16));
+    if (vec) {
+        int64_t threads = (n + 1) / 2;
+        unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
+        unary_v2<Op><<<blocks, kThreads, 0, s>>>(x0, x1, z0, z1, n);
+    } else {
+        unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
+        unary_v1<Op><<<blocks, kThreads, 0, s>>>(x0, x1, z0, z1, n);
+    }
+    return launch_status();
+}
+
+template <class Op>
+int run_binary(const double* x0, const double* x1, const double* y0, const double* y1, double* z0, double* z1,
+               int64_t n, void* stream) {
+    if (n < 0 || n > kMaxN) return TF_ERR_SIZE;
+    if (n == 0) return TF_OK;
+    if (!x0 || !y0 || !z0 || !z1) return TF_ERR_NULL;
+    if (!al(x0, 8) || !al(y0, 8) || !al(z0, 8) || !al(z1, 8) || (x1 && !al(x1, 8)) || (y1 && !al(y1, 8)))
+        return TF_ERR_ALIGN;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bool vec = al(x0, 16) && al(y0, 16) && al(z0, 16) && al(z1, 16) && (!x1 || al(x1, 16)) && (!y1 || al(y1, 16));
+    if (vec) {
+        int64_t threads = (n + 1) / 2;
+        unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
+        binary_v2<Op><<<blocks, kThreads, 0, s>>>(x0, x1, y0, y1, z0, z1, n);
+    } else {
+        unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
+        binary_v1<Op><<<blocks, kThreads, 0, s>>>(x0, x1, y0, y1, z0, z1, n);
+    }
+    return launch_status();
+}
+
+}  // namespace
+
+extern "C" {
+
+int tf_texp(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpExp>(x0, x1, z0, z1, n, stream);
+}
+int tf_texpm1(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpExpm1>(x0, x1, z0, z1, n, stream);
+}
+int tf_tlog(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpLog>(y0, y1, z0, z1, n, stream);
+}
+int tf_tlog1p(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpLog1p>(y0, y1, z0, z1, n, stream);
+}
+int tf_tadd(const double* x0, const double* x1, const double* y0, const double* y1, double* z0, double* z1,
+            int64_t n, void* stream) {
+    return run_binary<OpAdd>(x0, x1, y0, y1, z0, z1, n, stream);
+}
+int tf_tmul(const double* x0, const double* x1, const double* y0, const double* y1, double* z0, double* z1,
+            int64_t n, void* stream) {
+    return run_binary<OpMul>(x0, x1, y0, y1, z0, z1, n, stream);
+}
+
+const char* tf_strerror(int code) {
+    switch (code) {
+        case TF_OK: return "ok";
+        case TF_ERR_NULL: return "a required pointer is NULL";
+        case TF_ERR_SIZE: return "n is negative or too large";
+        case TF_ERR_ALIGN: return "a pointer is not 8-byte aligned";
+        case TF_ERR_LAUNCH: return "kernel launch failed";
+        case TF_ERR_NODEVICE: return "no usable CUDA device";
+        case TF_ERR_ARG: return "invalid argument";
+        default: return "unknown error code";
+    }
+}
+
+int tf_version(void) { return (1 << 16) | 0; }
+
+}  // extern "C"

@@ -116,10 +116,102 @@ WORKLOADS = {
 }
 
 
-def workload(func: str, n: int, start: int = 0):
-    """(x0, x1[, y0, y1]) of the named function's n-element workload."""
+def _workload1(func: str, n: int, start: int):
     gen, seed = WORKLOADS[func]
     x = gen(n, seed, start)
     if func in ("tadd", "tmul"):
         return x + gen(n, seed + 1, start)
     return x
+
+
+def workload(func: str, n: int, start: int = 0, chunk: int = 1 << 21):
+    """(x0, x1[, y0, y1]) of the named function's n-element workload.  Large
+    workloads are drawn in chunks on a thread pool (each element depends on its
+    index only, so the chunking does not change any value)."""
+    if n <= chunk:
+        return _workload1(func, n, start)
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+    pieces = [(s, min(chunk, n - s)) for s in range(0, n, chunk)]
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        parts = list(ex.map(lambda p: _workload1(func, p[1], start + p[0]), pieces))
+    return tuple(np.concatenate([p[k] for p in parts]) for k in range(len(parts[0])))
+
+
+# ---------------------------------------------------------------------------------
+# Hard cases: arguments near the thresholds where the result overflows, turns
+# subnormal or underflows to zero, near 1 for the logarithm and near -1 for
+# log1p, x1 = 0 and |x1| = half an ulp of x0, and the IEEE special values.
+# The threshold values are properties of the functions (where e^x crosses the
+# double range), not of any method of computing them.
+# ---------------------------------------------------------------------------------
+
+EXP_OVERFLOW = 709.782712893384      # e^x >= 2^1024 - 2^970 above this
+EXP_UNDERFLOW = -745.1332191019412   # e^x rounds to 0 at or below this
+EXP_SUBNORMAL = -708.3964185322641   # e^x < 2^-1022 below this
+
+SPECIALS = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1.0, -1.0, 5e-324, -5e-324,
+                     2.2250738585072014e-308, 1.7976931348623157e308, -1.7976931348623157e308])
+
+
+def _half_ulp(x0: np.ndarray) -> np.ndarray:
+    """Half the spacing of doubles above |x0| (exactly representable)."""
+    with np.errstate(invalid="ignore", over="ignore"):
+        return (np.nextafter(np.abs(x0), np.inf) - np.abs(x0)) * 0.5
+
+
+def _mix(parts, seed, n, start, x1_scale):
+    """Concatenate the generated pieces, cut to n, and draw x1: 10% zero, 5%
+    exactly +-half an ulp, else x0*u*2^-x1_scale; the last elements pair the
+    special values with each other."""
+    x0 = np.concatenate(parts)[:n]
+    x1 = _perturb(x0, seed, n, start, x1_scale)
+    pick = uniform(seed, S_AUX, n, start)
+    sgn = np.where(uniform(seed, S_SIGN, n, start) < 0.5, -1.0, 1.0)
+    x1 = np.where(pick < 0.10, 0.0, x1)
+    x1 = np.where((pick >= 0.10) & (pick < 0.15), sgn * _half_ulp(x0), x1)
+    m = SPECIALS.shape[0]
+    k = min(n, m * m)
+    if k:
+        a = np.repeat(SPECIALS, m)[:k]
+        b = np.tile(SPECIALS, m)[:k] * 2.0**-60
+        x0[n - k:] = a
+        x1[n - k:] = b
+    return x0, x1
+
+
+def hard_cases(func: str, n: int, seed: int = 9, start: int = 0):
+    """(x0, x1) hard-case arguments of a unary twofold function."""
+    U = lambda s: uniform(seed, s, n, start)  # noqa: E731
+    w = 2.0**-10
+    if func in ("texp", "texpm1"):
+        parts = [
+            EXP_OVERFLOW + w * (2 * U(5) - 1),
+            EXP_UNDERFLOW + w * (2 * U(6) - 1),
+            EXP_SUBNORMAL + w * (2 * U(7) - 1),
+            EXP_UNDERFLOW + (EXP_SUBNORMAL - EXP_UNDERFLOW) * U(8),
+            _signs(seed, n, start) * np.exp2(-1074 + 1060 * U(9)),   # tiny arguments
+            -40.0 + 2 * U(10) - 745 * (U(11) < 0.3),                   # expm1 saturating to -1
+        ]
+        if func == "texpm1":
+            parts[5] = -(np.exp2(5.0 + 5.0 * U(10)))
+    elif func == "tlog":
+        parts = [
+            1.0 + _signs(seed, n, start) * np.exp2(-60 + 40 * U(5)),  # 1 +- 2^-20 and closer
+            np.exp2(-1074 + 52 * U(6)),                                  # subnormal y0
+            np.exp2(1000 + 24 * U(7) * 0.999),                           # near DBL_MAX
+            np.exp2(-1022 + 2044 * U(8)),
+            1.0 + np.floor(U(9) * 2**20) * 2.0**-52,                     # 1 + a few ulps
+        ]
+    elif func == "tlog1p":
+        parts = [
+            -1.0 + np.exp2(-53 + 52 * U(5)),                             # near -1
+            _signs(seed, n, start) * np.exp2(-1074 + 1060 * U(6)),     # tiny, incl. subnormal
+            np.exp2(900 + 123 * U(7) * 0.999),                           # huge
+            (2 * U(8) - 1) * 0.5 + 0.2,                                  # around the n = 0 band edges
+            np.exp2(-20 + 19 * U(9)) * _signs(seed, n, start),
+        ]
+    else:
+        raise KeyError(func)
+    k = -(-n // len(parts))
+    return _mix([p[:k] for p in parts], seed, n, start, 53)

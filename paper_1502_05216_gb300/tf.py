@@ -1,0 +1,205 @@
+"""Python binding of libtf.so (argument marshalling only).
+
+Every function takes float64 tensors on a CUDA device and enqueues the kernel
+on the current torch stream (or the given one); all the arithmetic happens in
+the CUDA kernels behind the C ABI of include/tf.h.  There is no CPU fallback:
+without the built library or a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lib = None
+_lock = threading.Lock()
+
+UNARY = ("texp", "texpm1", "tlog", "tlog1p")
+BINARY = ("tadd", "tmul")
+
+
+class TwofoldError(RuntimeError):
+    pass
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libtf.so (it must have been built: paper_1502_05216_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or _build.LIB
+        if not os.path.exists(p):
+            raise TwofoldError(f"{p} is missing: build it with python -m paper_1502_05216_gb300.build")
+        lib = ctypes.CDLL(p)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        for name in UNARY:
+            f = getattr(lib, "tf_" + name)
+            f.argtypes = [vp, vp, vp, vp, i64, vp]
+            f.restype = i32
+        for name in BINARY:
+            f = getattr(lib, "tf_" + name)
+            f.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
+            f.restype = i32
+        lib.tf_strerror.argtypes = [i32]
+        lib.tf_strerror.restype = ctypes.c_char_p
+        lib.tf_version.restype = i32
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(rc: int, name: str):
+    if rc != 0:
+        raise TwofoldError(f"tf_{name}: {load().tf_strerror(rc).decode()} (code {rc})")
+
+
+def _ptr(t, name, n, device):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.float64 or not t.is_cuda or t.device != device:
+        raise TypeError(f"{name} must be a float64 CUDA tensor on {device}")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return t.data_ptr()
+
+
+def _stream(stream, device):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return s.cuda_stream
+
+
+def _unary(name, x0, x1=None, out=None, stream=None):
+    import torch
+    n = x0.numel()
+    dev = x0.device
+    if out is None:
+        out = (torch.empty_like(x0), torch.empty_like(x0))
+    args = (_ptr(x0, "x0", n, dev), _ptr(x1, "x1", n, dev), _ptr(out[0], "z0", n, dev),
+            _ptr(out[1], "z1", n, dev))
+    _check(getattr(load(), "tf_" + name)(*args, n, _stream(stream, dev)), name)
+    return out
+
+
+def _binary(name, x0, x1, y0, y1, out=None, stream=None):
+    import torch
+    n = x0.numel()
+    dev = x0.device
+    if out is None:
+        out = (torch.empty_like(x0), torch.empty_like(x0))
+    args = (_ptr(x0, "x0", n, dev), _ptr(x1, "x1", n, dev), _ptr(y0, "y0", n, dev), _ptr(y1, "y1", n, dev),
+            _ptr(out[0], "z0", n, dev), _ptr(out[1], "z1", n, dev))
+    _check(getattr(load(), "tf_" + name)(*args, n, _stream(stream, dev)), name)
+    return out
+
+
+def texp(x0, x1=None, out=None, stream=None):
+    """(z0, z1) with z0 + z1 = e^(x0 + x1), z0 = RN(e^x0)."""
+    return _unary("texp", x0, x1, out, stream)
+
+
+def texpm1(x0, x1=None, out=None, stream=None):
+    """(z0, z1) with z0 + z1 = e^(x0 + x1) - 1, z0 = RN(e^x0 - 1)."""
+    return _unary("texpm1", x0, x1, out, stream)
+
+
+def tlog(y0, y1=None, out=None, stream=None):
+    """(z0, z1) with z0 + z1 = log(y0 + y1), z0 = RN(log y0)."""
+    return _unary("tlog", y0, y1, out, stream)
+
+
+def tlog1p(y0, y1=None, out=None, stream=None):
+    """(z0, z1) with z0 + z1 = log(1 + y0 + y1), z0 = RN(log1p y0)."""
+    return _unary("tlog1p", y0, y1, out, stream)
+
+
+def tadd(x0, x1, y0, y1, out=None, stream=None):
+    """(z0, z1) with z0 = x0 + y0 (plain) and z0 + z1 = (x0 + x1) + (y0 + y1)."""
+    return _binary("tadd", x0, x1, y0, y1, out, stream)
+
+
+def tmul(x0, x1, y0, y1, out=None, stream=None):
+    """(z0, z1) with z0 = x0 * y0 (plain) and z0 + z1 = (x0 + x1)(y0 + y1)."""
+    return _binary("tmul", x0, x1, y0, y1, out, stream)
+
+
+FUNCS = {"texp": texp, "texpm1": texpm1, "tlog": tlog, "tlog1p": tlog1p, "tadd": tadd, "tmul": tmul}
+
+
+class HostPipeline:
+    """End-to-end evaluation on host arrays: the arrays are cut into chunks, and
+    each chunk's host-to-device copy, kernel and device-to-host copy are
+    enqueued on one of ``depth`` streams in turn, so the copy engines of one
+    chunk overlap the kernels of the others.  Device staging buffers are
+    allocated once per pipeline and reused.  Host arrays should be pinned
+    (``torch.empty(..., pin_memory=True)``) for the copies to be asynchronous."""
+
+    def __init__(self, device="cuda", chunk: int = 1 << 22, depth: int = 3):
+        import torch
+        self.device = torch.device(device)
+        self.chunk = int(chunk)
+        self.depth = int(depth)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(self.depth)]
+        self.bufs = [[torch.empty(self.chunk, dtype=torch.float64, device=self.device) for _ in range(6)]
+                     for _ in range(self.depth)]
+        self.launches = 0
+
+    def run(self, name, *host_arrays, out=None):
+        """z0 + z1 = name(*host_arrays) into the pinned host pair ``out`` (allocated
+        when None).  Returns ``out`` after the last copy has landed."""
+        import torch
+        h = [None if a is None else (a if isinstance(a, torch.Tensor) else torch.from_numpy(a))
+             for a in host_arrays]
+        n = h[0].numel()
+        if out is None:
+            out = (torch.empty(n, dtype=torch.float64, pin_memory=True),
+                   torch.empty(n, dtype=torch.float64, pin_memory=True))
+        cur = torch.cuda.current_stream(self.device)
+        for st in self.streams:
+            st.wait_stream(cur)
+        for c, s in enumerate(range(0, n, self.chunk)):
+            e = min(n, s + self.chunk)
+            m = e - s
+            slot = c % self.depth
+            st = self.streams[slot]
+            b = self.bufs[slot]
+            with torch.cuda.stream(st):
+                dargs = []
+                for k, a in enumerate(h):
+                    if a is None:
+                        dargs.append(None)
+                    else:
+                        b[k][:m].copy_(a[s:e], non_blocking=True)
+                        dargs.append(b[k][:m])
+                FUNCS[name](*dargs, out=(b[4][:m], b[5][:m]), stream=st)
+                self.launches += 1
+                out[0][s:e].copy_(b[4][:m], non_blocking=True)
+                out[1][s:e].copy_(b[5][:m], non_blocking=True)
+        for st in self.streams:
+            st.synchronize()
+        return out
+
+
+_pipes = {}
+
+
+def call_host(name, *host_arrays, out=None, device="cuda"):
+    """End-to-end call on host arrays (numpy or CPU torch tensors, pinned for
+    speed): copy in, run the kernel, copy (z0, z1) back, pipelined over chunks
+    and streams (HostPipeline).  Returns CPU tensors (pinned when allocated here)."""
+    import torch
+    dev = torch.device(device)
+    key = (dev.type, dev.index if dev.index is not None else torch.cuda.current_device())
+    if key not in _pipes:
+        _pipes[key] = HostPipeline(dev)
+    return _pipes[key].run(name, *host_arrays, out=out)
