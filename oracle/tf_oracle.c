@@ -227,17 +227,28 @@ static void ox_log1p(double y0, double y1, double *Z0, double *Gh, double *Gl, d
     if (amb) *fl |= FL_AMBIG;
     if (isnan(y1)) { set_exact(NAN, Gh, Gl, fl); return; }
     if (isinf(*Z0)) { set_exact(0.0, Gh, Gl, fl); return; }
+    /* w = 1 + y0 held exactly as the binary128 pair wh + wl (Knuth's TwoSum):
+       1 + y0 alone would drop a tiny y0, and 1 + y0 + y1 can cancel to it. */
+    Q wh = (Q)1 + (Q)y0;
+    Q bv = wh - (Q)1;
+    Q wl = ((Q)1 - (wh - bv)) + ((Q)y0 - bv);
 #if TFO_PLANT == 3
     Q w = (Q)y0;                                   /* planted: wrong base for log1p */
 #else
-    Q w = (Q)1 + (Q)y0;
+    Q w = wh;
 #endif
     Q P;
-    Q s = w + (Q)y1;
-    if (!isinf(y1) && (s - w) == (Q)y1 && (Q)y1 < -w / 2) {
+    if (!isinf(y1) && (Q)y1 < -w / 2) {
+        /* y1 cancels most of 1 + y0: s = 1 + y0 + y1 with one rounding (wh + y1
+           is exact by Sterbenz) and log(s) directly, not log1p of a ratio near -1. */
+        Q s = (wh + (Q)y1) + wl;
         if (s < 0) { set_exact(NAN, Gh, Gl, fl); return; }
         if (s == 0) { set_exact(-INFINITY, Gh, Gl, fl); return; }
-        P = logf128(s) - logf128(w);
+        Q Fs = logf128(s);
+        Q G = Fs - (Q)*Z0;
+        put_g(G, Gh, Gl);
+        *A = (double)qabs(Fs);
+        return;
     } else {
         P = corr_log1p(y1, w, L, *Z0, &sp, &zs);
         if (sp) { set_exact(zs, Gh, Gl, fl); return; }
