@@ -163,6 +163,15 @@ static void ox_expm1(double x0, double x1, double *Z0, double *Gh, double *Gl, d
     if (isinf(x1) && x1 > 0) { set_exact(INFINITY, Gh, Gl, fl); return; }
     Q E = expf128((Q)x0);
     Q U = isinf(x1) ? -E : E * expm1f128((Q)x1);  /* e^x0 (e^x1 - 1) */
+    if (isnan(U)) {
+        /* e^x0 underflowed to 0 while e^x1 overflowed: the product is undefined,
+           so take expm1 at the binary128 sum x0 + x1 (exact here: both parts
+           are huge) */
+        Q F = expm1f128((Q)x0 + (Q)x1);
+        put_g(F - (Q)*Z0, Gh, Gl);
+        *A = (double)qabs(F);
+        return;
+    }
     /* (e^x0 - 1) - Z0: below x0 = -1 the binary128 expm1 has dropped the low bits
        of e^x0, so form it as e^x0 - (1 + Z0), with 1 + Z0 exact. */
     Q D = (x0 < -1.0) ? E - ((Q)1 + (Q)*Z0) : M - (Q)*Z0;

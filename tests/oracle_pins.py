@@ -313,20 +313,23 @@ def pin_arith(lib):
 @_hiprec
 def pin_cancellation(lib):
     """Twofold arguments whose parts cancel: 1 + y0 + y1 (log1p) or y0 + y1 (log)
-    far below the parts, including a y0 that 1 + y0 would round away.  The exact
-    sum comes from rationals, its log from decimal."""
+    far below the parts, including a y0 that 1 + y0 would round away, and exp
+    arguments whose parts are far apart or huge.  The exact sum comes from
+    rationals, its log or exp from decimal."""
     dbl_max = 1.7976931348623157e308
     cases = [("tlog1p", 5e-324, -1.0), ("tlog1p", 2.0**-60, -1.0), ("tlog1p", dbl_max, -dbl_max),
              ("tlog1p", 0.75, -1.5), ("tlog1p", -0.5, -0.25), ("tlog1p", 2.0**-30, -1.0 + 2.0**-40),
-             ("tlog", 1.0, -0.75), ("tlog", 3.0, -2.9999999999999996), ("tlog", 2.0**-1000, -2.0**-1001)]
+             ("tlog", 1.0, -0.75), ("tlog", 3.0, -2.9999999999999996), ("tlog", 2.0**-1000, -2.0**-1001),
+             ("texpm1", -dbl_max, dbl_max * 2.0**-60), ("texpm1", -800.0, 799.5)]
     fails = []
     c = _ctx(80)
     for func, y0, y1 in cases:
         r = oracle.evaluate(func, np.array([y0]), np.array([y1]), lib=lib)
         s = (Fraction(1) if func == "tlog1p" else Fraction(0)) + Fraction(y0) + Fraction(y1)
-        F = c.ln(c.divide(decimal.Decimal(s.numerator), decimal.Decimal(s.denominator)))
+        sd = c.divide(decimal.Decimal(s.numerator), decimal.Decimal(s.denominator))
+        F = c.ln(sd) if func in ("tlog", "tlog1p") else c.exp(sd) - (1 if func == "texpm1" else 0)
         got = c.add(c.add(_D(r.Z0[0]), _D(r.Gh[0])), _D(r.Gl[0]))
-        if abs(got - F) > abs(F) * decimal.Decimal(2) ** -104:
+        if got.is_nan() or abs(got - F) > abs(F) * decimal.Decimal(2) ** -104:
             fails.append(f"{func}({y0!r} + {y1!r}) = {got:.25e}, want {F:.25e}")
     return fails
 
