@@ -51,7 +51,7 @@ def check(tf, func, args, where, rate=0.99999):
     if func in BINARY:
         assert np.array_equal(z0.view(np.int64), orc.Z0.view(np.int64)) or \
             np.all((z0 == orc.Z0) | (np.isnan(z0) & np.isnan(orc.Z0))), f"{where}: z0 not bitwise"
-    return tfcheck.check(z0, z1, orc, "f64", rate, where)
+    return tfcheck.check(z0, z1, orc, "f64", rate, where, func, args)
 
 
 @pytest.mark.parametrize("func", UNARY + BINARY)
@@ -74,7 +74,7 @@ def test_dotted_argument(tf, func):
     x0, _ = I.workload(func, 2**14 + 5)
     z0, z1 = run(tf, func, x0, None)
     orc = oracle.evaluate(func, x0, None)
-    tfcheck.check(z0, z1, orc, "f64", 0.99999, f"{func} dotted")
+    tfcheck.check(z0, z1, orc, "f64", 0.99999, f"{func} dotted", func, (x0, None))
     # the main part depends on x0 only
     x0, x1 = I.workload(func, 2**14 + 5)
     w0, _ = run(tf, func, x0, x1)
@@ -183,5 +183,5 @@ def test_full_size_sampled(tf, func):
     h1 = z1[ti].cpu().numpy()
     sub = [a[idx] for a in args]
     orc = oracle.evaluate(func, *sub)
-    st = tfcheck.check(h0, h1, orc, "f64", 0.99999, f"{func} 2^26 sampled")
+    st = tfcheck.check(h0, h1, orc, "f64", 0.99999, f"{func} 2^26 sampled", func, sub)
     print(func, st)
