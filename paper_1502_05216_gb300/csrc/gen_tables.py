@@ -16,8 +16,16 @@ split into doubles hi + lo (+ lo2) with hi = RN(v), lo = RN(v - hi).
       n*L0 is exact for |n| < 2^11 (the n ln2 term of the logarithm).
   TF_INV_C  256/ln2 rounded to double.
   TF_RF[m]  1/m! as (hi, lo), m = 0 .. 12 (Taylor coefficients of e^r).
+
+Fixed-point constants of the integer exp core (unsigned integers, rounded to
+nearest, each with its unit):
+  TF_TFIX[j]   2^(j/256), units 2^-127, as (lo64, hi64), j = -128 .. 128
+  TF_HC128_m   1/(m+2)!, units 2^-128, m = 0 .. 3 (Horner of (e^r - 1 - r)/r^2)
+  TF_HC64_m    1/(m+2)!, units 2^-72, m = 4 .. 8
+  TF_C12FIX    ln2/256 - C0, units 2^-148 (the tail of the reduction constant)
 """
 import decimal
+import math
 import sys
 
 D = decimal.Decimal
@@ -71,6 +79,31 @@ def main(out=sys.stdout):
         h, l = split(CTX.divide(1, f))
         w(f"#define TF_RF{m}_HI {hexd(h)}\n#define TF_RF{m}_LO {hexd(l)}\n")
     w("\n")
+    def fixed(v, unit_exp):
+        """round(v * 2^unit_exp) as a Python int (v a Decimal)."""
+        return int(CTX.multiply(v, CTX.power(2, unit_exp)).to_integral_value(rounding=decimal.ROUND_HALF_EVEN))
+
+    def u128(x):
+        assert 0 <= x < 2**128
+        return f"0x{x & (2**64 - 1):016x}ull, 0x{x >> 64:016x}ull"
+
+    w("/* fixed-point constants of the integer exp core */\n")
+    f = D(1)
+    for m in range(0, 9):
+        fact = D(math.factorial(m + 2))
+        v = CTX.divide(1, fact)
+        if m <= 3:
+            w(f"#define TF_HC128_{m} {{{u128(fixed(v, 128))}}}\n")
+        else:
+            w(f"#define TF_HC64_{m} 0x{fixed(v, 72):016x}ull\n")
+    c12 = CTX.subtract(c, D(C0))
+    w(f"#define TF_C12FIX {{{u128(fixed(c12, 148))}}}\n\n")
+    w("/* 2^(j/256) in units of 2^-127 as {lo64, hi64}; index j + 128 */\n")
+    w("TF_TABLE_QUALIFIER unsigned long long TF_TFIX_TABLE[257][2] = {\n")
+    for j in range(-128, 129):
+        v = CTX.power(D(2), CTX.divide(D(j), 256))
+        w(f"  {{{u128(fixed(v, 127))}}},\n")
+    w("};\n\n")
     for name, minus1 in (("TF_T", False), ("TF_E1", True)):
         w(f"/* {'2^(j/256) - 1' if minus1 else '2^(j/256)'} as hi, lo; index j + 128 */\n")
         w(f"TF_TABLE_QUALIFIER double {name}_TABLE[257][2] = {{\n")
