@@ -1,0 +1,165 @@
+// tf_fixed.cuh -- 128-bit fixed-point arithmetic on the integer pipes.
+//
+// On a GB300 the FP64 pipe issues 2 thread-instructions per SM per cycle while
+// the integer multiply-add (IMAD.WIDE.U32, 32 x 32 -> 64 bits) issues ~64, so
+// the long Taylor evaluation of the exp core (paper, "Twofold exponent" >
+// "Method summary": a Horner scheme carried to 2x precision) runs here in
+// unsigned 128-bit fixed point, and only the argument reduction, the 2^k
+// rescale and the twofold corrections stay in FP64.
+//
+// Every routine is exact integer arithmetic; truncations are stated where they
+// happen.  A value v held "in units 2^-u" is the integer round_down(v 2^u).
+#pragma once
+
+#include <cstdint>
+
+namespace tf {
+
+struct u128 {
+    uint64_t lo, hi;
+};
+
+// a * b + c with a 64-bit addend: one IMAD.WIDE.U32.
+__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+// Full 64 x 64 -> 128-bit product from four 32-bit partial products.  The
+// middle sums cannot overflow: (2^32 - 1)^2 + 2 (2^32 - 1) < 2^64.
+__device__ __forceinline__ u128 mul_full(uint64_t a, uint64_t b) {
+    uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+    uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    uint64_t p00 = mad_wide(a0, b0, 0ull);
+    uint64_t m1 = mad_wide(a0, b1, p00 >> 32);
+    uint64_t m2 = mad_wide(a1, b0, (uint32_t)m1);
+    uint64_t hi = mad_wide(a1, b1, m1 >> 32) + (m2 >> 32);
+    return {(m2 << 32) | (uint32_t)p00, hi};
+}
+
+__device__ __forceinline__ uint64_t mul_hi(uint64_t a, uint64_t b) { return mul_full(a, b).hi; }
+
+__device__ __forceinline__ u128 add128(u128 a, u128 b) {
+    u128 r;
+    asm("add.cc.u64 %0, %2, %4;\n\taddc.u64 %1, %3, %5;"
+        : "=l"(r.lo), "=l"(r.hi)
+        : "l"(a.lo), "l"(a.hi), "l"(b.lo), "l"(b.hi));
+    return r;
+}
+
+__device__ __forceinline__ u128 sub128(u128 a, u128 b) {
+    u128 r;
+    asm("sub.cc.u64 %0, %2, %4;\n\tsubc.u64 %1, %3, %5;"
+        : "=l"(r.lo), "=l"(r.hi)
+        : "l"(a.lo), "l"(a.hi), "l"(b.lo), "l"(b.hi));
+    return r;
+}
+
+__device__ __forceinline__ u128 add128_64(u128 a, uint64_t b) { return add128(a, {b, 0ull}); }
+
+// Two's complement negation.
+__device__ __forceinline__ u128 neg128(u128 a) { return sub128({0ull, 0ull}, a); }
+
+__device__ __forceinline__ bool is_neg128(u128 a) { return (int64_t)a.hi < 0; }
+
+__device__ __forceinline__ u128 sel128(bool p, u128 a, u128 b) { return {p ? a.lo : b.lo, p ? a.hi : b.hi}; }
+
+// c + t or c - t by the sign flag.
+__device__ __forceinline__ u128 addsub128(u128 c, u128 t, bool minus) {
+    return minus ? sub128(c, t) : add128(c, t);
+}
+
+// Logical shift right by a compile-time 0 <= s < 64.
+template <int s>
+__device__ __forceinline__ u128 shr128(u128 a) {
+    if constexpr (s == 0) {
+        return a;
+    } else {
+        return {(a.lo >> s) | (a.hi << (64 - s)), a.hi >> s};
+    }
+}
+
+// Logical shift right by a run-time 0 <= s < 64.
+__device__ __forceinline__ u128 shr128_var(u128 a, int s) {
+    uint64_t carry = (a.hi << 1) << (63 - s);  // a.hi << (64 - s), 0 for s == 0
+    return {(a.lo >> s) | carry, a.hi >> s};
+}
+
+// Logical shift left by a run-time 0 <= s <= 127.
+__device__ __forceinline__ u128 shl128_var(u128 a, int s) {
+    if (s >= 64) return {0ull, a.lo << (s - 64)};
+    uint64_t carry = (a.lo >> 1) >> (63 - s);  // a.lo >> (64 - s), 0 for s == 0
+    return {a.lo << s, (a.hi << s) | carry};
+}
+
+// A 53-bit (or shorter) integer m shifted by s bits, left for s >= 0 and right
+// (truncating) for s < 0; s <= 74 keeps the result below 2^127.
+__device__ __forceinline__ u128 place53(uint64_t m, int s) {
+    uint64_t lo = (s >= 0) ? ((s < 64) ? (m << s) : 0ull) : ((s > -64) ? (m >> -s) : 0ull);
+    uint64_t hi = (s >= 64) ? (m << (s - 64)) : ((s > 0) ? ((m >> 1) >> (63 - s)) : 0ull);
+    return {lo, hi};
+}
+
+// (a * b) >> (128 + s) for a, b < 2^128, 0 <= s < 64, from the three leading
+// partial products: the dropped low product a.lo * b.lo and the low halves of
+// the cross products make the result at most 3 units too small.  The caller
+// keeps a.hi * b.hi below 2^127 so that the sum cannot overflow.
+template <int s>
+__device__ __forceinline__ u128 mulshift(u128 a, u128 b) {
+    u128 p = mul_full(a.hi, b.hi);
+    p = add128_64(p, mul_hi(a.hi, b.lo));
+    p = add128_64(p, mul_hi(a.lo, b.hi));
+    return shr128<s>(p);
+}
+
+// a * n for a < 2^128 and a 32-bit n whose product stays below 2^128.
+__device__ __forceinline__ u128 mul128_u32(u128 a, uint32_t n) {
+    uint64_t p0 = mad_wide((uint32_t)a.lo, n, 0ull);
+    uint64_t p1 = mad_wide((uint32_t)(a.lo >> 32), n, p0 >> 32);
+    uint64_t p2 = mad_wide((uint32_t)a.hi, n, p1 >> 32);
+    uint64_t p3 = mad_wide((uint32_t)(a.hi >> 32), n, p2 >> 32);
+    return {(p1 << 32) | (uint32_t)p0, (p3 << 32) | (uint32_t)p2};
+}
+
+// The top 128 bits of the 181-bit product m * b (m < 2^53): (m b) >> 64.
+__device__ __forceinline__ u128 mul53_top(uint64_t m, u128 b) {
+    return add128_64(mul_full(m, b.hi), mul_hi(m, b.lo));
+}
+
+// ---------------------------------------------------------------------------
+// Fixed point -> twofold.  hi + lo = (-1)^neg M 2^E with hi = RN(M 2^E) (ties
+// to even) and lo = RN of the remainder, which is kept to 64 bits: |hi + lo -
+// M 2^E| <= 2^-115 |hi|.  M == 0 gives (+-0, 0).  The caller guarantees that
+// both parts are normal doubles (2^-960 <= M 2^E < 2^1023).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void to_pair(u128 M, int E, bool neg, double& hi, double& lo) {
+    const uint64_t sgn = neg ? 0x8000000000000000ull : 0ull;
+    bool zero = (M.hi | M.lo) == 0;
+    int lz = (M.hi != 0) ? __clzll((long long)M.hi) : 64 + __clzll((long long)(M.lo | 1ull));
+    u128 Mn = shl128_var(M, lz);  // bit 127 set
+    int L = 127 - lz;              // position of the leading bit of M
+    uint64_t m53 = Mn.hi >> 11;
+    bool rb = (Mn.hi >> 10) & 1;
+    bool st = ((Mn.hi & 0x3ffull) | Mn.lo) != 0;
+    bool up = rb && (st || (m53 & 1));
+    int be = E + L + 1023;  // biased exponent of the leading bit
+    uint64_t hib = ((uint64_t)(int64_t)(be - 1) << 52) + m53 + (up ? 1ull : 0ull);
+    // remainder: bits 74 .. 11 of Mn, weight of bit 11 = 2^(E + L - 116); rounding
+    // up leaves W - 2^64 (W >= 2^63 then), which is -(2^64 - W)
+    uint64_t W = (Mn.hi << 53) | (Mn.lo >> 11);
+    uint64_t mag = up ? (0ull - W) : W;
+    uint64_t lsg = up ? (sgn ^ 0x8000000000000000ull) : sgn;
+    int lz2 = __clzll((long long)(mag | 1ull));
+    uint64_t mn = mag << lz2;
+    uint64_t lm53 = mn >> 11;
+    bool lrb = (mn >> 10) & 1;
+    bool lst = (mn & 0x3ffull) != 0;
+    bool lup = lrb && (lst || (lm53 & 1));
+    int lbe = E + L - 116 + (63 - lz2) + 1023;
+    uint64_t lob = ((uint64_t)(int64_t)(lbe - 1) << 52) + lm53 + (lup ? 1ull : 0ull);
+    hi = __longlong_as_double((long long)((zero ? 0ull : hib) | sgn));
+    lo = __longlong_as_double((long long)((mag == 0 || zero) ? 0ull : (lob | lsg)));
+}
+
+}  // namespace tf
