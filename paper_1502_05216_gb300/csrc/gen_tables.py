@@ -2,13 +2,10 @@
 
 Run:  python gen_tables.py > tf_tables.h   (the build checks the file is current)
 
-All values come from Python's decimal module at 120 significant digits; a
-value split into doubles is hi = RN(v), lo = RN(v - hi).
+All values come from Python's decimal module at 120 significant digits.
 
   TF_C0     ln2/256 rounded down to 35 significant bits, so that N*C0 is exact
       for |N| < 2^19 (argument reduction x = N ln2/256 + r).
-  TF_L0, TF_L1, TF_L2  ln2 = L0 + L1 + L2, L0 with 42 significant bits so that
-      n*L0 is exact for |n| < 2^11 (the n ln2 term of the logarithm).
   TF_INV_C  256/ln2 rounded to double.
 
 Fixed-point constants of the integer exp core (unsigned integers, rounded to
@@ -20,6 +17,13 @@ nearest, each with its unit):
   TF_HC_m      1/(m+1)!, the coefficients of H(r) = (e^r - 1)/r = sum r^m/(m+1)!:
       m = 0 .. 4 in units 2^-127 as (lo64, hi64), m = 5 .. 9 in units 2^-72.
   TF_C12FIX    ln2/256 - C0 (> 0), units 2^-148: the tail of the reduction constant.
+  TF_LN2FIX    ln2, units 2^-128 (the n ln2 term of the logarithm).
+  TF_LOGTAB[i] for i = 724 .. 1448 (z = i/1024 covers [sqrt(1/2), sqrt(2))):
+      {log(c_i) in units 2^-64 (two's complement), C_i} with c_i = C_i 2^-24,
+      C_i = round(2^34 / i): the reciprocal table of the 1x logarithm seed,
+      log z = log1p(z c_i - 1) - log c_i with |z c_i - 1| < 2^-10.4.
+  TF_LG_m      (-1)^m / (m+1), m = 0 .. 5, units 2^-62 (two's complement): the
+      coefficients of log1p(t)/t.
 """
 import decimal
 import math
@@ -27,15 +31,6 @@ import sys
 
 D = decimal.Decimal
 CTX = decimal.Context(prec=120, Emax=99999, Emin=-99999)
-
-
-def split(v, n=2):
-    out = []
-    for _ in range(n):
-        h = float(v)  # correctly rounded
-        out.append(h)
-        v = CTX.subtract(v, D(h))
-    return out
 
 
 def trunc_bits(v, bits):
@@ -54,8 +49,6 @@ def main(out=sys.stdout):
     ln2 = CTX.ln(D(2))
     c = CTX.divide(ln2, 256)
     C0 = trunc_bits(c, 35)
-    L0 = trunc_bits(ln2, 42)
-    L1, L2 = split(CTX.subtract(ln2, D(L0)), 2)
     inv_c = float(CTX.divide(256, ln2))
     w = out.write
     w("/* Generated by gen_tables.py -- do not edit.  Constants of the twofold exp/log\n"
@@ -65,7 +58,7 @@ def main(out=sys.stdout):
     w(f"#define TF_TAB_HALF 128       /* table index j = -128 .. 128, step ln2/256 */\n")
     w(f"#define TF_INV_C {hexd(inv_c)}  /* 256/ln2 */\n")
     w(f"#define TF_C0 {hexd(C0)}\n")
-    w(f"#define TF_L0 {hexd(L0)}\n#define TF_L1 {hexd(L1)}\n#define TF_L2 {hexd(L2)}\n\n")
+    w("\n")
     def fixed(v, unit_exp):
         """round(v * 2^unit_exp) as a Python int (v a Decimal)."""
         return int(CTX.multiply(v, CTX.power(2, unit_exp)).to_integral_value(rounding=decimal.ROUND_HALF_EVEN))
@@ -87,6 +80,20 @@ def main(out=sys.stdout):
     c12 = CTX.subtract(c, D(C0))
     assert c12 > 0
     w(f"#define TF_C12FIX {{{u128(fixed(c12, 148))}}}\n\n")
+    w(f"#define TF_LN2FIX {{{u128(fixed(ln2, 128))}}}\n\n")
+    w("/* coefficients (-1)^m/(m+1) of log1p(t)/t, units 2^-62, two's complement */\n")
+    for m in range(0, 6):
+        x = fixed(CTX.divide(D((-1) ** m), D(m + 1)), 62)
+        w(f"#define TF_LG_{m} ((long long)0x{x & (2**64 - 1):016x}ull)\n")
+    w("\n#define TF_LOGTAB_LO 724\n#define TF_LOGTAB_HI 1448\n")
+    w("/* {log(c_i) units 2^-64 (two's complement), C_i} for i = 724 .. 1448, c_i = C_i 2^-24 */\n")
+    w("TF_TABLE_QUALIFIER long long TF_LOGTAB[725][2] = {\n")
+    for i in range(724, 1449):
+        C = int(CTX.divide(D(2**34), D(i)).to_integral_value(rounding=decimal.ROUND_HALF_EVEN))
+        lc = fixed(CTX.ln(CTX.divide(D(C), D(2**24))), 64)
+        assert abs(lc) < 2**63 and C < 2**25
+        w(f"  {{(long long)0x{lc & (2**64 - 1):016x}ull, {C}}},\n")
+    w("};\n\n")
     w("/* 2^(j/256) in units of 2^-127 as {lo64, hi64}; index j + 128 */\n")
     w("TF_TABLE_QUALIFIER unsigned long long TF_TFIX_TABLE[257][2] = {\n")
     for j in range(-128, 129):

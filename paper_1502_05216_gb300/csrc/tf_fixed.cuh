@@ -122,6 +122,26 @@ __device__ __forceinline__ u128 mul128_u32(u128 a, uint32_t n) {
     return {(p1 << 32) | (uint32_t)p0, (p3 << 32) | (uint32_t)p2};
 }
 
+// (a * n) >> s for a < 2^128, a 32-bit n and 0 < s < 64, from the full
+// 160-bit product; the caller keeps the result below 2^128.
+template <int s>
+__device__ __forceinline__ u128 mul128_u32_shr(u128 a, uint32_t n) {
+    uint64_t p0 = mad_wide((uint32_t)a.lo, n, 0ull);
+    uint64_t p1 = mad_wide((uint32_t)(a.lo >> 32), n, p0 >> 32);
+    uint64_t p2 = mad_wide((uint32_t)a.hi, n, p1 >> 32);
+    uint64_t p3 = mad_wide((uint32_t)(a.hi >> 32), n, p2 >> 32);
+    uint64_t lo = (p1 << 32) | (uint32_t)p0, hi = (p3 << 32) | (uint32_t)p2, top = p3 >> 32;
+    return {(lo >> s) | (hi << (64 - s)), (hi >> s) | (top << (64 - s))};
+}
+
+// High 64 bits of the signed 128-bit product of two signed 64-bit integers.
+__device__ __forceinline__ int64_t mul_hi_s(int64_t a, int64_t b) {
+    uint64_t h = mul_hi((uint64_t)a, (uint64_t)b);
+    h -= (a < 0) ? (uint64_t)b : 0ull;
+    h -= (b < 0) ? (uint64_t)a : 0ull;
+    return (int64_t)h;
+}
+
 // The top 128 bits of the 181-bit product m * b (m < 2^53): (m b) >> 64.
 __device__ __forceinline__ u128 mul53_top(uint64_t m, u128 b) {
     return add128_64(mul_full(m, b.hi), mul_hi(m, b.lo));
