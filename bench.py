@@ -38,16 +38,24 @@ WORKLOAD = ("texp, texpm1, tlog, tlog1p (+ tadd, tmul) over double twofolds, n=2
             "log1p half |x0| log-uniform in [2^-40, 2^-10), half -1+2^-30 .. 2^100; x1 = x0*u*2^-53")
 
 # FP64 pipe instructions (DADD + DMUL + DFMA, thread level) per element of each
-# kernel on its workload: the algorithmic work of the FP64-bound kernels.  Counted
-# with ncu (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum / n).
-FP64_PER_ELEM = {"texp": 71.0, "texpm1": 78.0, "tlog": 130.0, "tlog1p": 135.0, "tadd": 5.0, "tmul": 5.0}
-FP64_COUNT_SOURCE = "source count (not yet checked with ncu)"
+# kernel on its workload: ncu smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}
+# _pred_on.sum.per_cycle_elapsed x sm__cycles_elapsed.avg / n, from one
+# --set full capture at n = 2^25 (profiles/unary_v2_intcore_n2p25.md); tadd/tmul
+# are counted from the source (5 each).
+FP64_PER_ELEM = {"texp": 10.0, "texpm1": 12.0, "tlog": 26.5, "tlog1p": 31.9, "tadd": 5.0, "tmul": 5.0}
+FP64_COUNT_SOURCE = "ncu SASS counters (unary kernels), source count (tadd/tmul)"
 # HBM bytes per element: SoA doubles in + out.
 BYTES_PER_ELEM = {"texp": 32, "texpm1": 32, "tlog": 32, "tlog1p": 32, "tadd": 48, "tmul": 48}
-# DRAM traffic per launch from one ncu capture (dram__bytes_read.sum + write.sum),
-# None when no capture of the current kernels exists.
-TRAFFIC_PER_LAUNCH = {}
-
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# same capture at n = 2^25, scaled by 2 to the benchmark's n = 2^26 (the traffic
+# of an elementwise kernel is proportional to n).  The writes still held in L2 when
+# a launch ends are not in its count.
+TRAFFIC_PER_LAUNCH = {"texp": 2.0483e9, "texpm1": 2.0461e9, "tlog": 2.0457e9, "tlog1p": 2.0490e9}
+TRAFFIC_N = 1 << 26
+# Pipe utilisation of the same capture (sm__inst_executed_pipe_{fp64,alu}, % of
+# peak while active): the kernels are co-limited by the FP64 and integer pipes.
+PIPES = {"texp": {"fp64_pct": 55.6, "alu_pct": 78.3}, "texpm1": {"fp64_pct": 60.4, "alu_pct": 80.5},
+         "tlog": {"fp64_pct": 56.5, "alu_pct": 56.0}, "tlog1p": {"fp64_pct": 60.4, "alu_pct": 53.8}}
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -299,7 +307,9 @@ def ours(a, world, rank, local):
             "unit": "FP64 Ginst/s", "frac": achieved / (peak / 1e9),
             "peak_source": f"measured: DFMA calibration kernel on this GPU ({sms} SMs)",
             "fp64_inst_per_elem": FP64_PER_ELEM[dom], "fp64_count_source": FP64_COUNT_SOURCE,
-            "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+            "traffic": TRAFFIC_PER_LAUNCH.get(dom) if n == TRAFFIC_N else None,
+            "traffic_source": "ncu dram bytes of one launch at n=2^25, x2" if n == TRAFFIC_N else None,
+            "ncu_pipes_pct": PIPES.get(dom),
             "hbm_view": {"achieved_gbs": BYTES_PER_ELEM[dom] * n / d / 1e9, "peak_gbs": 6804.4,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}
     per = {f: {"ms": kern_ms[f], "gelem_s": n / (kern_ms[f] * 1e-3) / 1e9,
