@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--log2n", type=int, default=26)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-chains", action="store_true", help="skip the batched-chains measurement")
     ap.add_argument("--funcs", default=",".join(FUNCS),
                     help="comma-separated subset (for profiling a single kernel)")
     return ap.parse_args()
@@ -209,6 +210,29 @@ def fp64_peak(dev):
     return best, sms
 
 
+CHAIN_WORKLOAD = ("65,536 independent chains, lengths geometric (mean 256, cap 4096), ops uniform over "
+                  "{tadd, tmul, texp, tlog} (infeasible draws redrawn), states in [2^-20, 2^20], double twofolds")
+
+
+def chains_bench(dev):
+    """The batched-chains workload: one fused persistent launch (autotuned block
+    size and grid) against one launch per step and op kind, each captured in a
+    CUDA graph together with the reset of the chain states; median of 5 replays."""
+    from paper_1502_05216_gb300 import chains, inputs as I
+    batch = I.chains(65536)
+    cb = chains.ChainBatch(batch, dev)
+    cfg, table = cb.tune()
+    fused = cb.time_graph(cb.graph("fused", cfg["threads"], cfg["blocks"]), 5)
+    per_op = cb.time_graph(cb.graph("per_op"), 5)
+    ops = cb.total_ops
+    return {"workload": CHAIN_WORKLOAD, "ops": ops, "mix": dict(zip(("tadd", "tmul", "texp", "tlog"),
+                                                                    batch["mix"].tolist())),
+            "max_len": cb.max_len, "fused_ms": fused, "per_op_ms": per_op, "speedup": per_op / fused,
+            "fused_gops_s": ops / (fused * 1e-3) / 1e9, "fused_config": cfg,
+            "per_op_launches": cb.per_op_launches,
+            "tuning": [[r["threads"], r["blocks"], round(r["ms"], 3)] for r in table]}
+
+
 def ours(a, world, rank, local):
     global FUNCS
     FUNCS = tuple(f for f in a.funcs.split(",") if f)
@@ -315,6 +339,7 @@ def ours(a, world, rank, local):
     per = {f: {"ms": kern_ms[f], "gelem_s": n / (kern_ms[f] * 1e-3) / 1e9,
                "fp64_frac": FP64_PER_ELEM[f] * n / (kern_ms[f] * 1e-3) / peak,
                "hbm_gbs": BYTES_PER_ELEM[f] * n / (kern_ms[f] * 1e-3) / 1e9} for f in FUNCS}
+    chain = None if a.no_chains else chains_bench(dev)
     cpu = None
     if world == 1 and not a.no_cpu_baseline:
         rate, cores, sample, _, _ = oracle_rate(12.0)
@@ -326,7 +351,7 @@ def ours(a, world, rank, local):
         "config": {"workload": WORKLOAD, "n": n, "functions": list(FUNCS),
                    "l2": "no flush: every input array (512 MiB) is larger than L2", "parallelism": f"dp{world}"},
         "roofline": roof, "per_func": per, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": len(FUNCS) * a.steps, "clocks": ck,
+        "gpu_launches": len(FUNCS) * a.steps, "clocks": ck, "chains": chain,
     }), flush=True)
 
 

@@ -95,6 +95,53 @@ int tf_tadd(const double* x0, const double* x1, const double* y0, const double* 
 int tf_tmul(const double* x0, const double* x1, const double* y0, const double* y1,
             double* z0, double* z1, int64_t n, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Chains of twofold operations (the paper's on-the-fly error tracking: a
+ * twofold carries its deviation z1 through a whole computation, "Overview";
+ * here many independent computations run at once).
+ *
+ * A batch holds n_chains independent chains.  Chain c starts from the twofold
+ * state s = s0[c] + s1[c] and applies len[c] operations in order; operation t
+ * of chain c is ops[k] with operand a = a0[k] + a1[k], k = step_base[t] + c:
+ *   TF_OP_ADD  s <- tadd(s, a)      TF_OP_MUL  s <- tmul(s, a)
+ *   TF_OP_EXP  s <- texp(s)         TF_OP_LOG  s <- tlog(s)   (a unused)
+ * each exactly as the elementwise entry points compute it.  Layout ("step
+ * major"): the chains are numbered by non-increasing length, so the chains
+ * still running at step t are 0 .. active(t) - 1, and step t's operations are
+ * the contiguous block ops/a0/a1[step_base[t] .. step_base[t] + active(t)),
+ * with step_base[0] = 0 and step_base[t + 1] = step_base[t] + active(t).
+ * step_base has max_len + 1 entries (the last is the total number of
+ * operations).  s0/s1 are updated in place and hold the final states on
+ * return.  All pointers are device pointers owned by the caller.  An unknown
+ * op code leaves the state unchanged.
+ * ------------------------------------------------------------------------ */
+enum { TF_OP_ADD = 0, TF_OP_MUL = 1, TF_OP_EXP = 2, TF_OP_LOG = 3 };
+
+/* Bytes of device workspace tf_chain needs (the work-queue counter). */
+#define TF_CHAIN_WORKSPACE 256
+
+/* All chains in one persistent launch: each warp takes the next 32 chains
+ * from an atomic work queue (a counter in `workspace`, reset by this call with
+ * an asynchronous memset on `stream`) and runs them to the end, so short and
+ * long chains balance across the GPU; no thread ever waits on another.
+ * threads: block size, a multiple of 32 in [32, 1024] that the kernel's register
+ * use allows (TF_ERR_ARG otherwise; 512 always fits); blocks: grid size, <= 0
+ * for one wave of resident blocks (capped at what n_chains can use).
+ * workspace: TF_CHAIN_WORKSPACE bytes of device memory, 8-byte aligned,
+ * owned by the caller and used by no other call in flight (concurrent calls
+ * need separate workspaces).  len must be 4-byte aligned, the double and
+ * int64 arrays 8-byte aligned.  Returns TF_ERR_ARG for a bad block size,
+ * TF_ERR_NULL / TF_ERR_SIZE / TF_ERR_ALIGN as the other calls. */
+int tf_chain(const uint8_t* ops, const double* a0, const double* a1, const int64_t* step_base,
+             const int32_t* len, double* s0, double* s1, int64_t n_chains, int32_t max_len,
+             void* workspace, int threads, int blocks, void* stream);
+
+/* One operation kind at one step, for the chains listed in idx[0 .. n_idx)
+ * (the per-op baseline: one launch per step and operation kind): for each
+ * listed chain c, s[c] <- op(s[c], a[step_base_t + c]).  op is one of TF_OP_*. */
+int tf_chain_step(int op, const int32_t* idx, int64_t n_idx, int64_t step_base_t, const double* a0,
+                  const double* a1, double* s0, double* s1, void* stream);
+
 /* Human-readable name of an error code (static storage, never NULL). */
 const char* tf_strerror(int code);
 

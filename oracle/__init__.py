@@ -61,6 +61,9 @@ def _bind(path: str):
     lib.tfo_eval.restype = ctypes.c_int
     lib.tfo_libq.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp]
     lib.tfo_libq.restype = ctypes.c_int
+    vp = ctypes.c_void_p
+    lib.tfo_chain.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.tfo_chain.restype = ctypes.c_int
     lib.tfo_threads.restype = ctypes.c_int
     lib.tfo_set_threads.argtypes = [ctypes.c_int]
     return lib
@@ -127,6 +130,26 @@ def evaluate(func: str, x0, x1=None, y0=None, y1=None, lib=None) -> Result:
                 Z0[i] = z
     fl &= ~np.uint32(FL_AMBIG)
     return Result(Z0, Gh, Gl, A, fl)
+
+
+def chain(batch: dict, lib=None):
+    """Exact result (binary128) of every chain of a step-major batch (the dict
+    of paper_1502_05216_gb300.inputs.chains) and its condition sum K: returns
+    (Fh, Fl, K), F = Fh + Fl to about 106 bits; a computation that makes a
+    relative error of at most eps per operation is within eps K |F| of F."""
+    lib = lib or load()
+    n = batch["s0"].shape[0]
+    ops = np.ascontiguousarray(batch["ops"], dtype=np.uint8)
+    arr = {k: np.ascontiguousarray(batch[k], dtype=np.float64) for k in ("a0", "a1", "s0", "s1")}
+    sb = np.ascontiguousarray(batch["step_base"], dtype=np.int64)
+    ln = np.ascontiguousarray(batch["length"], dtype=np.int32)
+    Fh, Fl, K = np.empty(n), np.empty(n), np.empty(n)
+    p = lambda a: a.ctypes.data  # noqa: E731
+    rc = lib.tfo_chain(n, p(ops), p(arr["a0"]), p(arr["a1"]), p(sb), p(ln), p(arr["s0"]), p(arr["s1"]),
+                       p(Fh), p(Fl), p(K))
+    if rc != 0:
+        raise ValueError("tfo_chain rejected its arguments")
+    return Fh, Fl, K
 
 
 def libq(func: str, x) -> np.ndarray:

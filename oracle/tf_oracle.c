@@ -55,7 +55,7 @@
  * aarch64, which would change the plain double tadd/tmul main parts.)
  */
 #define _GNU_SOURCE 1
-/* TFO_PLANT=k compiles a deliberately wrong oracle (k = 1..7) so that the tests
+/* TFO_PLANT=k compiles a deliberately wrong oracle (k = 1..9) so that the tests
    can show their pins catch that kind of mistake.  Never set in normal builds. */
 #ifndef TFO_PLANT
 #define TFO_PLANT 0
@@ -353,6 +353,55 @@ int tfo_eval(int kind, int64_t n, const double *x0, const double *x1,
         case K_ADD:   ox_add(x0[i], a1, y0[i], y1 ? y1[i] : 0.0, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i]); break;
         case K_MUL:   ox_mul(x0[i], a1, y0[i], y1 ? y1[i] : 0.0, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i]); break;
         }
+    }
+    return 0;
+}
+
+/* Chains of twofold operations (the on-the-fly error tracking of the paper's
+   "Overview": the state carries its deviation through a whole computation).
+   For each chain, the exact result of its operations applied in order to the
+   exact initial state s0 + s1, evaluated in binary128 on the exact operands:
+       add: s + (a0 + a1)   mul: s (a0 + a1)   exp: e^s   log: log s
+   returned as Fh + Fl (about 106 bits), and the condition sum K of the chain:
+   if every operation makes a relative error of at most eps and the later
+   operations propagate it exactly, the final relative error is at most
+   eps K.  The relative-error gain of one operation on its input state is
+   |s| / |s + a| (add), 1 (mul), |s| (exp), 1 / |log s| (log), and
+   K = sum over steps t of the product of the gains after step t, accumulated
+   as k <- gain k + 1.  Layout as tf_chain (include/tf.h): operation t of
+   chain c is entry step_base[t] + c.  An unknown op code leaves the state. */
+int tfo_chain(int64_t n_chains, const uint8_t *ops, const double *a0, const double *a1,
+              const int64_t *step_base, const int32_t *len, const double *s0, const double *s1,
+              double *Fh, double *Fl, double *K)
+{
+    if (n_chains < 0) return -1;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t c = 0; c < n_chains; c++) {
+        Q s = (Q)s0[c] + (Q)s1[c];
+        double k = 0.0;
+        for (int32_t t = 0; t < len[c]; t++) {
+            int64_t i = step_base[t] + c;
+            Q a = (Q)a0[i] + (Q)a1[i];
+            double g = 1.0;
+            switch (ops[i]) {
+            case 0: { Q r = s + a; g = (double)(qabs(s) / qabs(r)); s = r; break; }
+#if TFO_PLANT == 8
+            case 1: s = s * (Q)a0[i]; break;            /* planted: drop the operand tail */
+#else
+            case 1: s = s * a; break;
+#endif
+            case 2: g = (double)qabs(s); s = expf128(s); break;
+            case 3: { Q r = logf128(s); g = (double)(1 / qabs(r)); s = r; break; }
+            default: k -= 1.0; break;   /* no operation, no error */
+            }
+#if TFO_PLANT == 9
+            k = k + 1.0;                                 /* planted: ignore the gains */
+#else
+            k = g * k + 1.0;
+#endif
+        }
+        put_g(s, &Fh[c], &Fl[c]);
+        K[c] = k;
     }
     return 0;
 }

@@ -21,7 +21,7 @@ LIBDIR = os.path.join(PKG, "_lib")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 LIB = os.path.join(LIBDIR, "libtf.so")
 PROBE_LIB = os.path.join(LIBDIR, "libtfprobe.so")
-SOURCES = ["tf_capi.cu"]
+SOURCES = ["tf_capi.cu", "tf_chain.cu"]
 PROBE_SOURCES = ["tf_probe.cu"]
 HEADERS = ["tf_core.cuh", "tf_eft.cuh", "tf_fixed.cuh", "tf_tables.h", os.path.join(INCLUDE, "tf.h"),
            os.path.join(INCLUDE, "tf_probe.h")]

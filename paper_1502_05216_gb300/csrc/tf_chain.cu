@@ -1,0 +1,172 @@
+// tf_chain.cu -- chains of twofold operations on sm_103a: one persistent fused
+// launch per batch, and the per-operation step kernels of the baseline.
+//
+// A chain carries its twofold state s0 + s1 through a sequence of tadd, tmul,
+// texp and tlog (the paper's on-the-fly error tracking, "Overview").  Each
+// operation is the same device code as the elementwise entry points; only the
+// warp votes are off in the fused kernel, whose lanes run different operations.
+//
+// Layout ("step major", see include/tf.h): chains are numbered longest first,
+// so at step t the running chains are 0 .. active(t) - 1 and their operations
+// are one contiguous block starting at step_base[t].  A warp that runs 32
+// consecutive chains therefore loads each step's op codes and operands with
+// coalesced accesses.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tf.h"
+#include "tf_core.cuh"
+
+namespace {
+
+// One operation on a chain's state; an unknown op code leaves it unchanged.
+__device__ __forceinline__ void apply_op(int op, double a0, double a1, double& s0, double& s1) {
+    double z0 = s0, z1 = s1;
+    switch (op) {
+        case TF_OP_ADD: tf::tadd1(s0, s1, a0, a1, z0, z1); break;
+        case TF_OP_MUL: tf::tmul1(s0, s1, a0, a1, z0, z1); break;
+        case TF_OP_EXP: tf::texp_impl<false, true>(s0, s1, z0, z1); break;
+        case TF_OP_LOG: tf::tlog_impl<false>(s0, s1, z0, z1); break;
+        default: break;
+    }
+    s0 = z0;
+    s1 = z1;
+}
+
+// Persistent fused kernel.  Lane 0 of each warp takes the next 32 chains from
+// the work queue (one atomicAdd, no waiting); the warp runs them to the end and
+// takes more until the queue is empty.  Chains come longest first, so the long
+// chains start early and the short ones fill in behind them.
+__global__ void chain_fused(const uint8_t* __restrict__ ops, const double* __restrict__ a0,
+                            const double* __restrict__ a1, const int64_t* __restrict__ step_base,
+                            const int32_t* __restrict__ len, double* s0, double* s1, int64_t n_chains,
+                            unsigned long long* queue) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long start = 0;
+        if (lane == 0) start = atomicAdd(queue, 32ull);
+        start = __shfl_sync(0xffffffffu, start, 0);
+        if (start >= (unsigned long long)n_chains) break;
+        int64_t c = (int64_t)start + lane;
+        bool in = c < n_chains;
+        int L = in ? len[c] : 0;
+        double x0 = in ? s0[c] : 0.0, x1 = in ? s1[c] : 0.0;
+        for (int t = 0; t < L; ++t) {
+            int64_t k = __ldg(step_base + t) + c;
+            apply_op(__ldg(ops + k), __ldg(a0 + k), __ldg(a1 + k), x0, x1);
+        }
+        if (in) {
+            s0[c] = x0;
+            s1[c] = x1;
+        }
+    }
+}
+
+struct StepAdd {
+    static constexpr double dummy = 0.0;
+    __device__ static void eval(double x0, double x1, double y0, double y1, double& z0, double& z1) {
+        tf::tadd1(x0, x1, y0, y1, z0, z1);
+    }
+};
+struct StepMul {
+    static constexpr double dummy = 0.0;
+    __device__ static void eval(double x0, double x1, double y0, double y1, double& z0, double& z1) {
+        tf::tmul1(x0, x1, y0, y1, z0, z1);
+    }
+};
+struct StepExp {
+    static constexpr double dummy = 0.0;
+    __device__ static void eval(double x0, double x1, double, double, double& z0, double& z1) {
+        tf::texp1(x0, x1, z0, z1);
+    }
+};
+struct StepLog {
+    static constexpr double dummy = 1.0;
+    __device__ static void eval(double x0, double x1, double, double, double& z0, double& z1) {
+        tf::tlog1(x0, x1, z0, z1);
+    }
+};
+
+// One operation kind over the listed chains.  Every lane of a warp runs the
+// operation (lanes past the end on a dummy state, storing nothing) so that the
+// warp votes of texp/tlog see full warps.
+template <class Op>
+__global__ void __launch_bounds__(256) chain_step_kernel(const int32_t* __restrict__ idx, int64_t n,
+                                                        int64_t sb, const double* __restrict__ a0,
+                                                        const double* __restrict__ a1, double* s0, double* s1) {
+    int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    bool in = i < n;
+    int64_t c = in ? idx[i] : 0;
+    double x0 = in ? s0[c] : Op::dummy, x1 = in ? s1[c] : 0.0;
+    double y0 = in ? a0[sb + c] : 1.0, y1 = in ? a1[sb + c] : 0.0;
+    double z0, z1;
+    Op::eval(x0, x1, y0, y1, z0, z1);
+    if (in) {
+        s0[c] = z0;
+        s1[c] = z1;
+    }
+}
+
+int launch_status() {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return TF_OK;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return TF_ERR_NODEVICE;
+    return TF_ERR_LAUNCH;
+}
+
+inline bool al8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int tf_chain(const uint8_t* ops, const double* a0, const double* a1, const int64_t* step_base,
+             const int32_t* len, double* s0, double* s1, int64_t n_chains, int32_t max_len, void* workspace,
+             int threads, int blocks, void* stream) {
+    if (n_chains < 0 || max_len < 0 || n_chains > ((int64_t)1 << 40)) return TF_ERR_SIZE;
+    if (threads < 32 || threads > 1024 || (threads & 31)) return TF_ERR_ARG;
+    if (n_chains == 0 || max_len == 0) return TF_OK;
+    if (!ops || !a0 || !a1 || !step_base || !len || !s0 || !s1 || !workspace) return TF_ERR_NULL;
+    if (!al8(a0) || !al8(a1) || !al8(step_base) || !al8(s0) || !al8(s1) || !al8(workspace) ||
+        (reinterpret_cast<uintptr_t>(len) & 3))
+        return TF_ERR_ALIGN;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, chain_fused) != cudaSuccess) return launch_status() == TF_OK ? TF_ERR_LAUNCH : launch_status();
+    if (threads > fa.maxThreadsPerBlock) return TF_ERR_ARG;  // the kernel's registers do not fit
+    if (blocks <= 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain_fused, threads, 0) != cudaSuccess)
+            return launch_status() == TF_OK ? TF_ERR_LAUNCH : launch_status();
+        blocks = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    int64_t need = (n_chains + threads - 1) / threads;  // more blocks than chains/threads would idle
+    if (blocks > need) blocks = (int)need;
+    if (cudaMemsetAsync(workspace, 0, sizeof(unsigned long long), s) != cudaSuccess) return launch_status();
+    chain_fused<<<blocks, threads, 0, s>>>(ops, a0, a1, step_base, len, s0, s1, n_chains,
+                                           static_cast<unsigned long long*>(workspace));
+    return launch_status();
+}
+
+int tf_chain_step(int op, const int32_t* idx, int64_t n_idx, int64_t step_base_t, const double* a0,
+                  const double* a1, double* s0, double* s1, void* stream) {
+    if (op < TF_OP_ADD || op > TF_OP_LOG) return TF_ERR_ARG;
+    if (n_idx < 0 || n_idx > ((int64_t)1 << 40) || step_base_t < 0) return TF_ERR_SIZE;
+    if (n_idx == 0) return TF_OK;
+    if (!idx || !a0 || !a1 || !s0 || !s1) return TF_ERR_NULL;
+    if (!al8(a0) || !al8(a1) || !al8(s0) || !al8(s1) || (reinterpret_cast<uintptr_t>(idx) & 3)) return TF_ERR_ALIGN;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned grid = (unsigned)((n_idx + 255) / 256);
+    switch (op) {
+        case TF_OP_ADD: chain_step_kernel<StepAdd><<<grid, 256, 0, s>>>(idx, n_idx, step_base_t, a0, a1, s0, s1); break;
+        case TF_OP_MUL: chain_step_kernel<StepMul><<<grid, 256, 0, s>>>(idx, n_idx, step_base_t, a0, a1, s0, s1); break;
+        case TF_OP_EXP: chain_step_kernel<StepExp><<<grid, 256, 0, s>>>(idx, n_idx, step_base_t, a0, a1, s0, s1); break;
+        default: chain_step_kernel<StepLog><<<grid, 256, 0, s>>>(idx, n_idx, step_base_t, a0, a1, s0, s1); break;
+    }
+    return launch_status();
+}
+
+}  // extern "C"

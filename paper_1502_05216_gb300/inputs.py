@@ -215,3 +215,91 @@ def hard_cases(func: str, n: int, seed: int = 9, start: int = 0):
         raise KeyError(func)
     k = -(-n // len(parts))
     return _mix([p[:k] for p in parts], seed, n, start, 53)
+
+
+# ---------------------------------------------------------------------------------
+# Batched chains of twofold operations (step-major layout of include/tf.h).
+# ---------------------------------------------------------------------------------
+
+OP_ADD, OP_MUL, OP_EXP, OP_LOG = 0, 1, 2, 3
+# streams of the chain draws (each draw has its own)
+_C_LEN, _C_INIT, _C_OP, _C_OPFIX, _C_MAG, _C_PERT = 10, 11, 12, 13, 14, 15
+_LO, _HI = 2.0**-20, 2.0**20
+_EXP_MAX = 20.0 * math.log(2.0)                # e^s <= 2^20
+_LOG_MIN = math.exp(2.0**-20)                  # log s >= 2^-20
+
+
+def chains(n_chains: int, seed: int = 8, mean_len: float = 256.0, cap: int = 4096):
+    """A batch of independent chains whose ops are drawn uniformly from
+    {tadd, tmul, texp, tlog} and whose states stay in [2^-20, 2^20] (positive):
+
+    * length L = min(1 + Geom(p = 1/mean_len), cap) (geometric with that mean);
+    * initial state s0 uniform in [1, 2), s1 = s0 u 2^-53;
+    * at each step the op is drawn uniformly; an op that would leave the range
+      (texp with e^s > 2^20, tlog with log s < 2^-20, tadd with no room above s)
+      is redrawn uniformly among the feasible ones;
+    * tadd operand a0 log-uniform in [2^-20, 2^20 - s] (positive: no
+      cancellation); tmul operand a0 = t / s with t log-uniform in
+      [2^-20, 2^20]; a1 = a0 u 2^-53; texp/tlog carry a0 = a1 = 0.
+
+    The host follows each state in plain double only to decide feasibility.
+    Chains are numbered longest first; the op stream is step-major.  Returns a
+    dict: ops (uint8), a0, a1 (float64), step_base (int64, max_len + 1),
+    length (int32), s0, s1 (float64), max_len, mix (count per op)."""
+    if n_chains <= 0:
+        raise ValueError("n_chains must be positive")
+    p = 1.0 / mean_len
+    u = uniform(seed, _C_LEN, n_chains)
+    L = 1 + np.floor(np.log1p(-u) / math.log1p(-p))
+    L = np.minimum(L, cap).astype(np.int64)
+    order = np.argsort(-L, kind="stable")       # longest first; ties by index
+    L = L[order]
+    max_len = int(L[0])
+    s0 = 1.0 + uniform(seed, _C_INIT, n_chains)[order]
+    s1 = s0 * (2 * uniform(seed, _C_PERT, n_chains)[order] - 1) * 2.0**-53
+    active = np.searchsorted(-L, -np.arange(max_len), side="left")  # chains with L > t
+    step_base = np.zeros(max_len + 1, dtype=np.int64)
+    step_base[1:] = np.cumsum(active)
+    total = int(step_base[-1])
+    ops = np.empty(total, dtype=np.uint8)
+    a0 = np.zeros(total)
+    a1 = np.zeros(total)
+    s = s0.copy()
+    for t in range(max_len):
+        m = int(active[t])
+        ids = order[:m].astype(np.uint64) * np.uint64(cap) + np.uint64(t)   # per (chain, step) counter
+        ids = ids.astype(np.int64)
+        st = s[:m]
+        U = lambda stream: _uniform_at(seed, stream, ids)  # noqa: E731
+        feas = np.stack([st <= _HI - _LO, np.ones(m, bool), st <= _EXP_MAX, st >= _LOG_MIN], axis=1)
+        op = np.minimum((U(_C_OP) * 4).astype(np.int64), 3)
+        bad = ~feas[np.arange(m), op]
+        if bad.any():  # redraw uniformly among the feasible ops
+            nf = feas[bad].sum(axis=1)
+            pick = np.minimum((U(_C_OPFIX)[bad] * nf).astype(np.int64), nf - 1)
+            cum = np.cumsum(feas[bad], axis=1)
+            op[bad] = np.argmax(cum > pick[:, None], axis=1)
+        mag = U(_C_MAG)
+        pert = 2 * U(_C_PERT) - 1
+        x = np.zeros(m)
+        add = op == OP_ADD
+        hi = np.log2(np.maximum(_HI - st[add], _LO))
+        x[add] = np.exp2(-20.0 + (hi + 20.0) * mag[add])
+        mu = op == OP_MUL
+        x[mu] = np.exp2(-20.0 + 40.0 * mag[mu]) / st[mu]
+        sl = slice(int(step_base[t]), int(step_base[t + 1]))
+        ops[sl] = op
+        a0[sl] = x
+        a1[sl] = x * pert * 2.0**-53
+        with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+            s[:m] = np.where(add, st + x, np.where(mu, st * x, np.where(op == OP_EXP, np.exp(st), np.log(st))))
+    mix = np.bincount(ops, minlength=4)
+    return {"ops": ops, "a0": a0, "a1": a1, "step_base": step_base, "length": L.astype(np.int32),
+            "s0": s0, "s1": s1, "max_len": max_len, "mix": mix}
+
+
+def _uniform_at(seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
+    """U in [0, 1) at arbitrary counter indices (same generator as uniform())."""
+    base = np.uint64((seed << 40) | (stream << 36))
+    c = idx.astype(np.uint64) + base
+    return (splitmix64(c) >> np.uint64(11)).astype(np.float64) * 2.0**-53

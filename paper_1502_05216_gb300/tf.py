@@ -47,6 +47,10 @@ def load(path: str | None = None):
             f = getattr(lib, "tf_" + name)
             f.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
             f.restype = i32
+        lib.tf_chain.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, ctypes.c_int32, vp, i32, i32, vp]
+        lib.tf_chain.restype = i32
+        lib.tf_chain_step.argtypes = [i32, vp, i64, i64, vp, vp, vp, vp, vp]
+        lib.tf_chain_step.restype = i32
         lib.tf_strerror.argtypes = [i32]
         lib.tf_strerror.restype = ctypes.c_char_p
         lib.tf_version.restype = i32
@@ -131,6 +135,52 @@ def tadd(x0, x1, y0, y1, out=None, stream=None):
 def tmul(x0, x1, y0, y1, out=None, stream=None):
     """(z0, z1) with z0 = x0 * y0 (plain) and z0 + z1 = (x0 + x1)(y0 + y1)."""
     return _binary("tmul", x0, x1, y0, y1, out, stream)
+
+
+# operation codes of the chain entry points (TF_OP_* in include/tf.h)
+OP_ADD, OP_MUL, OP_EXP, OP_LOG = 0, 1, 2, 3
+CHAIN_WORKSPACE = 256  # TF_CHAIN_WORKSPACE
+
+
+def _dptr(t, name, dtype, device):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or t.device != device:
+        raise TypeError(f"{name} must be a {dtype} CUDA tensor on {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def chain(ops, a0, a1, step_base, length, s0, s1, max_len, workspace, threads=128, blocks=0, stream=None):
+    """tf_chain: run every chain of a step-major batch to its end in one
+    persistent launch; s0/s1 (float64) are updated in place.  ops uint8,
+    step_base int64, length int32, workspace a uint8 tensor of
+    CHAIN_WORKSPACE bytes."""
+    import torch
+    dev = s0.device
+    n = s0.numel()
+    if s1.numel() != n or length.numel() != n or step_base.numel() != int(max_len) + 1:
+        raise ValueError("s0, s1, length must have one entry per chain; step_base max_len + 1")
+    if workspace.numel() * workspace.element_size() < CHAIN_WORKSPACE:
+        raise ValueError(f"workspace must hold {CHAIN_WORKSPACE} bytes")
+    args = (_dptr(ops, "ops", torch.uint8, dev), _dptr(a0, "a0", torch.float64, dev),
+            _dptr(a1, "a1", torch.float64, dev), _dptr(step_base, "step_base", torch.int64, dev),
+            _dptr(length, "length", torch.int32, dev), _dptr(s0, "s0", torch.float64, dev),
+            _dptr(s1, "s1", torch.float64, dev))
+    if not workspace.is_cuda or workspace.device != dev:
+        raise TypeError(f"workspace must be on {dev}")
+    _check(load().tf_chain(*args, n, int(max_len), workspace.data_ptr(), int(threads), int(blocks),
+                           _stream(stream, dev)), "chain")
+
+
+def chain_step(op, idx, step_base_t, a0, a1, s0, s1, stream=None):
+    """tf_chain_step: one operation kind at one step for the chains in idx (int32)."""
+    import torch
+    dev = s0.device
+    args = (_dptr(idx, "idx", torch.int32, dev), idx.numel(), int(step_base_t),
+            _dptr(a0, "a0", torch.float64, dev), _dptr(a1, "a1", torch.float64, dev),
+            _dptr(s0, "s0", torch.float64, dev), _dptr(s1, "s1", torch.float64, dev))
+    _check(load().tf_chain_step(int(op), *args, _stream(stream, dev)), "chain_step")
 
 
 FUNCS = {"texp": texp, "texpm1": texpm1, "tlog": tlog, "tlog1p": tlog1p, "tadd": tadd, "tmul": tmul}

@@ -334,5 +334,78 @@ def pin_cancellation(lib):
     return fails
 
 
+def _chain_batch(ops_list, a_list, s_init):
+    """A step-major batch (include/tf.h layout) from per-chain lists of op codes,
+    operands (a0, a1) and initial states (s0, s1); chains must be given
+    longest first."""
+    n = len(ops_list)
+    L = np.array([len(o) for o in ops_list], dtype=np.int32)
+    assert np.all(np.diff(L) <= 0)
+    max_len = int(L.max())
+    active = [int(np.sum(L > t)) for t in range(max_len)]
+    sb = np.zeros(max_len + 1, dtype=np.int64)
+    sb[1:] = np.cumsum(active)
+    ops = np.zeros(int(sb[-1]), dtype=np.uint8)
+    a0 = np.zeros(int(sb[-1]))
+    a1 = np.zeros(int(sb[-1]))
+    for c in range(n):
+        for t, op in enumerate(ops_list[c]):
+            k = sb[t] + c
+            ops[k] = op
+            a0[k], a1[k] = a_list[c][t]
+    s0 = np.array([s[0] for s in s_init])
+    s1 = np.array([s[1] for s in s_init])
+    return {"ops": ops, "a0": a0, "a1": a1, "step_base": sb, "length": L, "s0": s0, "s1": s1,
+            "max_len": max_len}
+
+
+@_hiprec
+def pin_chain_decimal(lib):
+    """Chains of the batched workload (short ones) against the same operations
+    applied in 80-digit decimal arithmetic to the exact inputs: the oracle's F
+    must agree to 2^-100 K relative (binary128 makes ~2^-112 per operation)."""
+    b = I.chains(300, seed=171, mean_len=8.0, cap=40)
+    Fh, Fl, K = oracle.chain(b, lib=lib)
+    ctx = _ctx(80)
+    fails = []
+    for c in range(b["s0"].shape[0]):
+        s = _D(b["s0"][c]) + _D(b["s1"][c])
+        for t in range(int(b["length"][c])):
+            k = int(b["step_base"][t]) + c
+            op = int(b["ops"][k])
+            a = _D(b["a0"][k]) + _D(b["a1"][k])
+            s = (s + a) if op == 0 else (s * a) if op == 1 else ctx.exp(s) if op == 2 else ctx.ln(s)
+        F = _D(Fh[c]) + _D(Fl[c])
+        if abs(F - s) > abs(s) * decimal.Decimal(2) ** -100 * decimal.Decimal(K[c]):
+            fails.append((c, float(F), float(s)))
+    return fails
+
+
+def pin_chain_condition(lib):
+    """The condition sum K in closed form (k <- gain k + 1 per operation): one
+    operation gives K = 1; exp then log gives 1/|log e^s| + 1 = 1/|s| + 1; an
+    add then a product gives 1 * 1 + 1 = 2.  And the values: log(exp(s)) = s,
+    (s + a) b and s b exactly."""
+    s = 0.75
+    b = _chain_batch([[2, 3], [0, 1], [1], [2], [3]],
+                     [[(0.0, 0.0), (0.0, 0.0)], [(0.25, 0.0), (3.0, 0.0)], [(2.0, 0.0)], [(0.0, 0.0)],
+                      [(0.0, 0.0)]],
+                     [(s, 0.0), (s, 0.0), (s, 0.0), (s, 0.0), (2.5, 0.0)])
+    Fh, Fl, K = oracle.chain(b, lib=lib)
+    fails = []
+    want = {0: 1.0 / s + 1.0, 1: 2.0, 2: 1.0, 3: 1.0, 4: 1.0}
+    for c, w in want.items():
+        if abs(K[c] - w) > 1e-12 * w:
+            fails.append(("K", c, K[c], w))
+    if abs(Fh[0] - s) > 2.0**-110 or abs((Fh[0] - s) + Fl[0]) > 2.0**-110:
+        fails.append(("log(exp(s))", Fh[0], Fl[0]))
+    if Fh[1] != 3.0 or Fl[1] != 0.0:            # (0.75 + 0.25) * 3 exactly
+        fails.append(("(s + a) b", Fh[1], Fl[1]))
+    if Fh[2] != 1.5 or Fl[2] != 0.0:
+        fails.append(("s b", Fh[2], Fl[2]))
+    return fails
+
+
 ALL_PINS = [pin_mainpart_decimal, pin_deviation_decimal, pin_closed_forms, pin_series,
-            pin_invariants, pin_special, pin_arith, pin_cancellation]
+            pin_invariants, pin_special, pin_arith, pin_cancellation, pin_chain_decimal,
+            pin_chain_condition]

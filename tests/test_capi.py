@@ -58,6 +58,22 @@ def test_error_codes_before_any_launch(lib):
         assert f(good, good, good, good, good, good, -3, None) == 2
         assert f(good, good, None, good, good, good, 3, None) == 1
         assert f(good, good, good, odd, good, good, 3, None) == 3
+    # chains: sizes, block size and op code are checked first
+    vp = ctypes.c_void_p
+    lib.tf_chain.argtypes = [vp] * 7 + [ctypes.c_int64, ctypes.c_int32, vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.tf_chain_step.argtypes = [ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int64] + [vp] * 5
+    g7 = [good] * 7
+    assert lib.tf_chain(*g7, 0, 5, good, 128, 0, None) == 0         # no chains: no-op
+    assert lib.tf_chain(*g7, -1, 5, good, 128, 0, None) == 2        # TF_ERR_SIZE
+    assert lib.tf_chain(*g7, 10, -1, good, 128, 0, None) == 2
+    assert lib.tf_chain(*g7, 10, 5, good, 33, 0, None) == 6         # TF_ERR_ARG: not a warp multiple
+    assert lib.tf_chain(*g7, 10, 5, good, 2048, 0, None) == 6
+    assert lib.tf_chain(*g7, 10, 5, None, 128, 0, None) == 1        # no workspace
+    assert lib.tf_chain(*g7, 10, 5, odd, 128, 0, None) == 3
+    assert lib.tf_chain_step(7, good, 5, 0, good, good, good, good, None) == 6
+    assert lib.tf_chain_step(0, good, 0, 0, good, good, good, good, None) == 0
+    assert lib.tf_chain_step(1, good, -2, 0, good, good, good, good, None) == 2
+    assert lib.tf_chain_step(2, None, 5, 0, good, good, good, good, None) == 1
     assert lib.tf_strerror(2).decode() == "n is negative or too large"
     assert lib.tf_strerror(12345).decode() == "unknown error code"
     assert lib.tf_version() >> 16 == 1

@@ -1,0 +1,174 @@
+"""Parity of the chain kernels (tf_chain, tf_chain_step) with the CPU oracle.
+
+A chain applies tadd/tmul/texp/tlog in sequence to a twofold state.  Checked:
+  * the fused persistent launch and the per-operation baseline give the same
+    final states bit for bit, under every launch configuration and in CUDA
+    graphs (both run the same device operations in the same order per chain);
+  * the final state z0 + z1 is within 2^-97 K |F| of the exact result F of
+    the chain, K its condition sum (oracle.chain): each operation makes a
+    relative error of at most ~2^-100 and the later ones propagate it;
+  * a chain of one operation equals the elementwise entry point bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_05216_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+EPS = 2.0**-97
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+    from paper_1502_05216_gb300 import build, chains, tf
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test collected on a machine without CUDA")
+    build.build()
+    tf.load()
+    return tf, chains
+
+
+def check_oracle(batch, z0, z1, where):
+    Fh, Fl, K = oracle.chain(batch)
+    # |z0 + z1 - F| with the large parts cancelled first
+    err = np.abs((z0 - Fh) + (z1 - Fl))
+    A = np.abs(Fh)
+    tol = EPS * K * A + 2.0**-1060
+    bad = np.nonzero(~(err <= tol))[0]
+    assert bad.size == 0, (f"{where}: {bad.size} chains beyond 2^-97 K |F|; first {bad[:5]}: "
+                           f"err/|F| {err[bad[:5]] / A[bad[:5]]}, K {K[bad[:5]]}")
+    rel = err / A
+    return {"chains": int(z0.size), "max_rel_log2": float(np.log2(rel.max())) if rel.max() > 0 else -np.inf,
+            "max_rel_over_K_log2": float(np.log2((rel / K).max())) if rel.max() > 0 else -np.inf,
+            "max_K_log2": float(np.log2(K.max()))}
+
+
+def run_both(chains, batch):
+    cb = chains.ChainBatch(batch)
+    cb.reset()
+    cb.run_fused()
+    f = cb.state()
+    cb.reset()
+    cb.run_per_op()
+    p = cb.state()
+    return cb, f, p
+
+
+def test_fused_equals_per_op_and_oracle(mods):
+    tf, chains = mods
+    batch = I.chains(4096, seed=21, mean_len=64.0, cap=512)
+    cb, f, p = run_both(chains, batch)
+    assert np.array_equal(f[0].view(np.int64), p[0].view(np.int64))
+    assert np.array_equal(f[1].view(np.int64), p[1].view(np.int64))
+    print(check_oracle(batch, *f, "4096 chains"))
+
+
+@pytest.mark.parametrize("threads,blocks", [(32, 0), (64, 1), (256, 0), (512, 3), (128, 1000)])
+def test_launch_configs_agree(mods, threads, blocks):
+    """Block size, grid size and the work queue change who runs a chain, never its result."""
+    tf, chains = mods
+    batch = I.chains(3000, seed=22, mean_len=32.0, cap=300)
+    cb = chains.ChainBatch(batch)
+    cb.reset()
+    cb.run_fused(128, 0)
+    ref = cb.state()
+    cb.reset()
+    cb.run_fused(threads, blocks)
+    got = cb.state()
+    assert np.array_equal(ref[0].view(np.int64), got[0].view(np.int64))
+    assert np.array_equal(ref[1].view(np.int64), got[1].view(np.int64))
+
+
+def test_too_large_block_is_rejected(mods):
+    """A block size whose registers do not fit is refused before launching."""
+    tf, chains = mods
+    batch = I.chains(64, seed=26, mean_len=4.0, cap=8)
+    cb = chains.ChainBatch(batch)
+    with pytest.raises(tf.TwofoldError, match="invalid argument"):
+        cb.run_fused(1024, 0)
+
+
+def test_graphs_replay(mods):
+    import torch
+    tf, chains = mods
+    batch = I.chains(2048, seed=23, mean_len=40.0, cap=400)
+    cb = chains.ChainBatch(batch)
+    cb.reset()
+    cb.run_fused()
+    ref = cb.state()
+    for mode in ("fused", "per_op"):
+        g = cb.graph(mode)
+        for _ in range(2):
+            cb.s0.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            got = cb.state()
+            assert np.array_equal(ref[0].view(np.int64), got[0].view(np.int64)), mode
+            assert np.array_equal(ref[1].view(np.int64), got[1].view(np.int64)), mode
+
+
+def test_single_op_chains_equal_elementwise(mods):
+    """A chain of length 1 is the elementwise function of its state and operand."""
+    import torch
+    tf, chains = mods
+    n = 1000
+    x0, x1 = I.exp_args(n, 31)
+    x0 = np.abs(x0) % 13.0 + 2.0**-20
+    x1 = x0 * (np.arange(n) % 7 - 3) * 2.0**-55
+    y0, y1 = I.arith_args(n, 32)
+    for op, name in ((0, "tadd"), (1, "tmul"), (2, "texp"), (3, "tlog")):
+        batch = {"ops": np.full(n, op, np.uint8), "a0": y0, "a1": y1, "step_base": np.array([0, n], np.int64),
+                 "length": np.ones(n, np.int32), "s0": x0, "s1": x1, "max_len": 1}
+        cb = chains.ChainBatch(batch)
+        cb.run_fused()
+        got = cb.state()
+        d = [torch.from_numpy(a).cuda() for a in ((x0, x1, y0, y1) if op < 2 else (x0, x1))]
+        z0, z1 = tf.FUNCS[name](*d)
+        assert np.array_equal(z0.cpu().numpy().view(np.int64), got[0].view(np.int64)), name
+        assert np.array_equal(z1.cpu().numpy().view(np.int64), got[1].view(np.int64)), name
+
+
+def test_edge_batches(mods):
+    """One chain; all chains of equal length; an unknown op code is a no-op."""
+    tf, chains = mods
+    b1 = I.chains(1, seed=24, mean_len=100.0, cap=200)
+    cb, f, p = run_both(chains, b1)
+    assert np.array_equal(f[0].view(np.int64), p[0].view(np.int64))
+    check_oracle(b1, *f, "one chain")
+    b2 = I.chains(500, seed=25, mean_len=1e9, cap=50)  # every chain hits the cap
+    assert np.all(b2["length"] == 50)
+    cb, f, p = run_both(chains, b2)
+    assert np.array_equal(f[1].view(np.int64), p[1].view(np.int64))
+    check_oracle(b2, *f, "equal lengths")
+    b3 = dict(b2)
+    b3["ops"] = b2["ops"].copy()
+    b3["ops"][b2["step_base"][49]:b2["step_base"][50]] = 200  # last step: unknown op everywhere
+    cb, f3, p3 = run_both(chains, b3)
+    assert np.array_equal(f3[0].view(np.int64), p3[0].view(np.int64))
+    check_oracle(b3, *f3, "unknown op")
+    b4 = dict(b2)
+    b4["ops"] = b2["ops"][:b2["step_base"][49]]
+    b4["step_base"] = b2["step_base"][:50]
+    b4["length"] = np.full(500, 49, np.int32)
+    b4["max_len"] = 49
+    cb = chains.ChainBatch(b4)
+    cb.run_fused()
+    f4 = cb.state()
+    assert np.array_equal(f3[0].view(np.int64), f4[0].view(np.int64))
+
+
+def test_full_size_batch(mods):
+    """The full batched-chains workload: 65,536 chains, mean length 256, cap
+    4096; every chain checked against the oracle, fused == per-op bitwise."""
+    tf, chains = mods
+    batch = I.chains(65536)
+    cb, f, p = run_both(chains, batch)
+    assert np.array_equal(f[0].view(np.int64), p[0].view(np.int64))
+    assert np.array_equal(f[1].view(np.int64), p[1].view(np.int64))
+    st = check_oracle(batch, *f, "65536 chains")
+    st["ops"] = int(batch["ops"].size)
+    st["mix"] = batch["mix"].tolist()
+    print(st)
