@@ -136,6 +136,30 @@ int tf_chain(const uint8_t* ops, const double* a0, const double* a1, const int64
              const int32_t* len, double* s0, double* s1, int64_t n_chains, int32_t max_len,
              void* workspace, int threads, int blocks, void* stream);
 
+/* tf_chain without the caller's workspace, for callers that cannot allocate
+ * device memory themselves: code that runs where a host framework owns all of
+ * the device's memory through its own pool or a hard cap, and code on a
+ * latency-critical path that cannot afford cudaMalloc, which may synchronize
+ * the whole device.  The paper has no counterpart; it is a deployment variant
+ * of tf_chain.
+ *
+ * The work-queue counter lives in a static device array of
+ * TF_CHAIN_NOALLOC_SCRATCH bytes inside the library, which every GPU that
+ * loads the library holds until the process exits.  This call allocates
+ * nothing: the first call on each device looks up that device's address of
+ * the array (cudaGetSymbolAddress, with the device current) and caches it, so
+ * make that first call before any stream capture.  Every call clears the
+ * counter on `stream` and then uses it; all calls share the one array, so
+ * calls whose work overlaps on the GPU (on different streams, or from
+ * different host threads) race on it and give wrong results: keep them
+ * ordered.  Arguments and results as tf_chain; n_chains above
+ * TF_CHAIN_NOALLOC_MAX_CHAINS returns TF_ERR_SIZE. */
+#define TF_CHAIN_NOALLOC_SCRATCH 256
+#define TF_CHAIN_NOALLOC_MAX_CHAINS (1LL << 40)
+int tf_chain_noalloc(const uint8_t* ops, const double* a0, const double* a1, const int64_t* step_base,
+                     const int32_t* len, double* s0, double* s1, int64_t n_chains, int32_t max_len,
+                     int threads, int blocks, void* stream);
+
 /* One operation kind at one step, for the chains listed in idx[0 .. n_idx)
  * (the per-op baseline: one launch per step and operation kind): for each
  * listed chain c, s[c] <- op(s[c], a[step_base_t + c]).  op is one of TF_OP_*. */

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "tf.h"
 #include "tf_core.cuh"
@@ -117,6 +118,36 @@ int launch_status() {
 
 inline bool al8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
 
+// Scratch of tf_chain_noalloc: the work-queue counter lives in this array,
+// which every device that loads the library holds until the process exits.
+// Host code must not pass the symbol itself to a kernel (on the host it only
+// stands for the device array); each device's address is looked up once.
+constexpr int kNoAllocScratchBytes = TF_CHAIN_NOALLOC_SCRATCH;
+static __device__ __align__(256) unsigned char g_chain_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_chain_scratch on the current device, looked up with
+// cudaGetSymbolAddress on the first call per device and cached.
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return launch_status() == TF_OK ? TF_ERR_NODEVICE : launch_status();
+    if (dev < 0 || dev >= kMaxDevices) return TF_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_chain_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();  // do not leave the error for an unrelated later check
+            return TF_ERR_LAUNCH;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return TF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -149,6 +180,20 @@ int tf_chain(const uint8_t* ops, const double* a0, const double* a1, const int64
     chain_fused<<<blocks, threads, 0, s>>>(ops, a0, a1, step_base, len, s0, s1, n_chains,
                                            static_cast<unsigned long long*>(workspace));
     return launch_status();
+}
+
+int tf_chain_noalloc(const uint8_t* ops, const double* a0, const double* a1, const int64_t* step_base,
+                     const int32_t* len, double* s0, double* s1, int64_t n_chains, int32_t max_len, int threads,
+                     int blocks, void* stream) {
+    if (n_chains < 0 || max_len < 0 || n_chains > TF_CHAIN_NOALLOC_MAX_CHAINS) return TF_ERR_SIZE;
+    if (threads < 32 || threads > 1024 || (threads & 31)) return TF_ERR_ARG;
+    if (n_chains == 0 || max_len == 0) return TF_OK;
+    void* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != TF_OK) return rc;
+    // the same launch as tf_chain with the static scratch as its workspace (tf_chain
+    // clears the queue counter on `stream` before launching)
+    return tf_chain(ops, a0, a1, step_base, len, s0, s1, n_chains, max_len, scratch, threads, blocks, stream);
 }
 
 int tf_chain_step(int op, const int32_t* idx, int64_t n_idx, int64_t step_base_t, const double* a0,

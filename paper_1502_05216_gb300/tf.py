@@ -49,6 +49,8 @@ def load(path: str | None = None):
             f.restype = i32
         lib.tf_chain.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, ctypes.c_int32, vp, i32, i32, vp]
         lib.tf_chain.restype = i32
+        lib.tf_chain_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, ctypes.c_int32, i32, i32, vp]
+        lib.tf_chain_noalloc.restype = i32
         lib.tf_chain_step.argtypes = [i32, vp, i64, i64, vp, vp, vp, vp, vp]
         lib.tf_chain_step.restype = i32
         lib.tf_strerror.argtypes = [i32]
@@ -171,6 +173,23 @@ def chain(ops, a0, a1, step_base, length, s0, s1, max_len, workspace, threads=12
         raise TypeError(f"workspace must be on {dev}")
     _check(load().tf_chain(*args, n, int(max_len), workspace.data_ptr(), int(threads), int(blocks),
                            _stream(stream, dev)), "chain")
+
+
+def chain_noalloc(ops, a0, a1, step_base, length, s0, s1, max_len, threads=128, blocks=0, stream=None):
+    """tf_chain_noalloc: as chain() but with the library's static scratch in
+    place of a workspace, for callers that cannot allocate device memory (see
+    include/tf.h); calls must not overlap on the GPU."""
+    import torch
+    dev = s0.device
+    n = s0.numel()
+    if s1.numel() != n or length.numel() != n or step_base.numel() != int(max_len) + 1:
+        raise ValueError("s0, s1, length must have one entry per chain; step_base max_len + 1")
+    args = (_dptr(ops, "ops", torch.uint8, dev), _dptr(a0, "a0", torch.float64, dev),
+            _dptr(a1, "a1", torch.float64, dev), _dptr(step_base, "step_base", torch.int64, dev),
+            _dptr(length, "length", torch.int32, dev), _dptr(s0, "s0", torch.float64, dev),
+            _dptr(s1, "s1", torch.float64, dev))
+    _check(load().tf_chain_noalloc(*args, n, int(max_len), int(threads), int(blocks), _stream(stream, dev)),
+           "chain_noalloc")
 
 
 def chain_step(op, idx, step_base_t, a0, a1, s0, s1, stream=None):
