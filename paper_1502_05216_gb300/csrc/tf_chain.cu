@@ -53,9 +53,35 @@ __global__ void chain_fused(const uint8_t* __restrict__ ops, const double* __res
         bool in = c < n_chains;
         int L = in ? len[c] : 0;
         double x0 = in ? s0[c] : 0.0, x1 = in ? s1[c] : 0.0;
+        // software pipeline: the op code and operand of step t + 1 (and the block
+        // base of step t + 2) are loaded before step t computes, so that a chain's
+        // sequential steps do not wait on memory
+        int op = 0;
+        double b0 = 0.0, b1 = 0.0;
+        int64_t sb1 = 0;
+        if (L > 0) {
+            int64_t k = __ldg(step_base) + c;
+            op = __ldg(ops + k);
+            b0 = __ldg(a0 + k);
+            b1 = __ldg(a1 + k);
+            sb1 = (L > 1) ? __ldg(step_base + 1) : 0;
+        }
         for (int t = 0; t < L; ++t) {
-            int64_t k = __ldg(step_base + t) + c;
-            apply_op(__ldg(ops + k), __ldg(a0 + k), __ldg(a1 + k), x0, x1);
+            int opn = 0;
+            double b0n = 0.0, b1n = 0.0;
+            int64_t sb2 = 0;
+            if (t + 1 < L) {
+                int64_t k = sb1 + c;
+                opn = __ldg(ops + k);
+                b0n = __ldg(a0 + k);
+                b1n = __ldg(a1 + k);
+                sb2 = (t + 2 < L) ? __ldg(step_base + t + 2) : 0;
+            }
+            apply_op(op, b0, b1, x0, x1);
+            op = opn;
+            b0 = b0n;
+            b1 = b1n;
+            sb1 = sb2;
         }
         if (in) {
             s0[c] = x0;
