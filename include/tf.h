@@ -48,7 +48,7 @@ enum {
     TF_OK = 0,
     TF_ERR_NULL = 1,     /* a required pointer is NULL */
     TF_ERR_SIZE = 2,     /* n < 0, or n beyond the supported range */
-    TF_ERR_ALIGN = 3,    /* a pointer is not 8-byte aligned */
+    TF_ERR_ALIGN = 3,    /* a pointer is not aligned to its element size */
     TF_ERR_LAUNCH = 4,   /* the kernel launch was rejected (cudaGetLastError) */
     TF_ERR_NODEVICE = 5, /* no usable CUDA device */
     TF_ERR_ARG = 6       /* another invalid argument (e.g. an unknown variant) */
@@ -80,6 +80,20 @@ int tf_tlog(const double* y0, const double* y1, double* z0, double* z1, int64_t 
  * (tlog1p, plog1p, tlog1p0): Newton step on e^x - 1.  z0 = RN(log1p y0);
  * y0 < -1 gives NaN, y0 = -1 gives -Inf (z1 = 0). */
 int tf_tlog1p(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
+
+/* Float twofolds: the same four functions over pairs of floats, with the
+ * paper's "f"-suffixed float variants in mind ("Twofold exponent" and
+ * "Twofold logarithm" give each algorithm for float and double).  Every
+ * pointer is a device float array of n elements; alignment 4 bytes (16 for
+ * the 128-bit vector kernel); otherwise the contract of the double entry
+ * points applies.  All arithmetic is float-float on the FP32 pipes, IEEE
+ * binary32 round to nearest, no flush of subnormals.  z0 = RN_float(f(x0));
+ * texpf overflows at x0 >= 88.72284 and underflows to 0 at x0 <= -103.97208;
+ * tlogf/tlog1pf as tlog/tlog1p. */
+int tf_texpf(const float* x0, const float* x1, float* z0, float* z1, int64_t n, void* stream);
+int tf_texpm1f(const float* x0, const float* x1, float* z0, float* z1, int64_t n, void* stream);
+int tf_tlogf(const float* y0, const float* y1, float* z0, float* z1, int64_t n, void* stream);
+int tf_tlog1pf(const float* y0, const float* y1, float* z0, float* z1, int64_t n, void* stream);
 
 /* Twofold sum z0 + z1 = (x0 + x1) + (y0 + y1).
  * Paper: "Overview" (z0 = x0 (+) y0, the ordinary double sum) and

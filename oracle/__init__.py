@@ -59,6 +59,9 @@ def _bind(path: str):
     lib.tfo_eval.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, dp, dp, dp, dp, dp, dp,
                              ctypes.POINTER(ctypes.c_uint)]
     lib.tfo_eval.restype = ctypes.c_int
+    lib.tfo_eval2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, dp, dp, dp, dp, dp, dp, dp, dp,
+                              ctypes.POINTER(ctypes.c_uint)]
+    lib.tfo_eval2.restype = ctypes.c_int
     lib.tfo_libq.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp]
     lib.tfo_libq.restype = ctypes.c_int
     vp = ctypes.c_void_p
@@ -109,22 +112,26 @@ class Result:
         self.Z0, self.Gh, self.Gl, self.A, self.flags = Z0, Gh, Gl, A, flags
 
 
-def evaluate(func: str, x0, x1=None, y0=None, y1=None, lib=None) -> Result:
-    """Oracle answer for every element of the twofold function ``func``."""
+def evaluate(func: str, x0, x1=None, y0=None, y1=None, lib=None, dtype: str = "f64") -> Result:
+    """Oracle answer for every element of the twofold function ``func``.
+    dtype "f32": float twofolds (unary functions; the float arguments are
+    exact in double), Z0 = f(x0) rounded to float."""
     lib = lib or load()
     kind = KINDS[func]
+    f32 = dtype == "f32"
     x0, x1, y0, y1 = map(_as_f64, (x0, x1, y0, y1))
     n = x0.shape[0]
     Z0, Gh, Gl, A = (np.empty(n) for _ in range(4))
     fl = np.empty(n, dtype=np.uint32)
-    rc = lib.tfo_eval(kind, n, _p(x0), _p(x1), _p(y0), _p(y1), _p(Z0), _p(Gh), _p(Gl), _p(A),
-                      fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint)))
+    rc = lib.tfo_eval2(kind, int(f32), n, _p(x0), _p(x1), _p(y0), _p(y1), _p(Z0), _p(Gh), _p(Gl), _p(A),
+                       fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint)))
     if rc != 0:
         raise ValueError(f"tfo_eval rejected its arguments ({rc})")
     amb = np.nonzero(fl & FL_AMBIG)[0]
+    rnd = round_to_float if f32 else round_to_double
     for i in amb:  # re-decide the rounding of f(x0) with 80 significant digits
         if func in ("texp", "texpm1", "tlog", "tlog1p"):
-            z = round_to_double(dec_f(func, float(x0[i]), 80))
+            z = rnd(dec_f(func, float(x0[i]), 80))
             if z != Z0[i]:
                 Gh[i] -= z - Z0[i]  # both are within one double spacing: exact shift
                 Z0[i] = z
@@ -185,6 +192,29 @@ def dec_f(func: str, x: float, digits: int = 60) -> decimal.Decimal:
     if func == "tlog1p":
         return ctx.ln(ctx.add(d, 1))  # 1 + x is exact at this precision
     raise KeyError(func)
+
+
+def round_to_float(v: decimal.Decimal) -> float:
+    """Nearest float (binary32, ties to even, subnormals, overflow at
+    2^128 - 2^103) of a decimal value, returned as a Python float."""
+    if v.is_nan():
+        return float("nan")
+    if v.is_infinite():
+        return float(v)
+    big = decimal.Decimal(2) ** 128 - decimal.Decimal(2) ** 103
+    if abs(v) >= big:
+        return float("inf") if v > 0 else float("-inf")
+    c = np.float32(float(v))
+    best = None
+    for x in (np.nextafter(c, np.float32(-np.inf)), c, np.nextafter(c, np.float32(np.inf))):
+        if not np.isfinite(x):
+            continue
+        d = abs(decimal.Decimal(float(x)) - v)
+        odd = int(np.array(x, dtype=np.float32).view(np.int32)) & 1
+        key = (d, odd)
+        if best is None or key < best[0]:
+            best = (key, float(x))
+    return best[1]
 
 
 def round_to_double(v: decimal.Decimal) -> float:

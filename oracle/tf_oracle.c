@@ -21,6 +21,7 @@
  *
  * Per element the oracle returns
  *   Z0    : f(x0) rounded to nearest double (ties to even, IEEE subnormals/overflow),
+ *           or to nearest float for float twofolds (tfo_eval2 with f32 = 1),
  *   G     : the ideal deviation F - Z0, F = f(x0 + x1), as a pair of doubles
  *           Gh + Gl (about 106 bits of G),
  *   A     : |F| rounded to double (the scale for relative errors),
@@ -55,7 +56,7 @@
  * aarch64, which would change the plain double tadd/tmul main parts.)
  */
 #define _GNU_SOURCE 1
-/* TFO_PLANT=k compiles a deliberately wrong oracle (k = 1..9) so that the tests
+/* TFO_PLANT=k compiles a deliberately wrong oracle (k = 1..10) so that the tests
    can show their pins catch that kind of mistake.  Never set in normal builds. */
 #ifndef TFO_PLANT
 #define TFO_PLANT 0
@@ -112,6 +113,48 @@ static double rn_double(Q F, int *ambig)
     return d;
 }
 
+/* Round a binary128 value to the nearest float (returned as a double) and flag
+ * values within 2^-50 of a float spacing from a rounding midpoint.  The
+ * binary128 -> binary32 conversion is one IEEE rounding. */
+static double rn_float(Q F, int *ambig)
+{
+#if TFO_PLANT == 10
+    float f = (float)(double)F;     /* planted: round through double, then toward zero */
+    if (isfinite(f) && qabs((Q)f) > qabs(F)) f = nextafterf(f, 0.0f);
+#else
+    float f = (float)F;
+#endif
+    *ambig = 0;
+    if (isnan(f) || isinf(F))
+        return (double)f;
+    Q a = qabs(F);
+    if (a == 0)
+        return (double)f;
+    float af = fabsf(f);
+    if (isinf(af))
+        af = FLT_MAX;
+    Q r = a - (Q)af;
+    Q spacing, mid;
+    if (r >= 0) {
+        float up = nextafterf(af, INFINITY);
+        spacing = isinf(up) ? (Q)ldexp(1.0, 104) : (Q)up - (Q)af;
+        mid = r - spacing / 2;
+    } else {
+        float dn = nextafterf(af, 0.0f);
+        spacing = (Q)af - (Q)dn;
+        mid = -r - spacing / 2;
+    }
+    if (qabs(mid) <= spacing * (Q)0x1p-50)
+        *ambig = 1;
+    return (double)f;
+}
+
+/* The main part: F rounded to the twofold's format (f32: binary32, else binary64). */
+static double rn_main(Q F, int *ambig, int f32)
+{
+    return f32 ? rn_float(F, ambig) : rn_double(F, ambig);
+}
+
 static void put_g(Q G, double *Gh, double *Gl)
 {
     double h = (double)G;
@@ -128,13 +171,13 @@ static void set_exact(double z1, double *Gh, double *Gl, unsigned *fl)
 
 /* ---- unary twofold functions --------------------------------------------------- */
 
-static void ox_exp(double x0, double x1, double *Z0, double *Gh, double *Gl, double *A, unsigned *fl)
+static void ox_exp(double x0, double x1, double *Z0, double *Gh, double *Gl, double *A, unsigned *fl, int f32)
 {
     int amb = 0;
     *fl = 0; *A = 0;
     if (isnan(x0)) { *Z0 = NAN; set_exact(NAN, Gh, Gl, fl); return; }
     Q E = expf128((Q)x0);                          /* e^x0; exp(-Inf) = 0, exp(+Inf) = Inf */
-    *Z0 = rn_double(E, &amb);
+    *Z0 = rn_main(E, &amb, f32);
     if (amb) *fl |= FL_AMBIG;
     if (isnan(x1)) { set_exact(NAN, Gh, Gl, fl); return; }
     if (*Z0 == 0.0 || isinf(*Z0)) { set_exact(0.0, Gh, Gl, fl); return; }
@@ -150,13 +193,13 @@ static void ox_exp(double x0, double x1, double *Z0, double *Gh, double *Gl, dou
     *A = (double)qabs(E + U);
 }
 
-static void ox_expm1(double x0, double x1, double *Z0, double *Gh, double *Gl, double *A, unsigned *fl)
+static void ox_expm1(double x0, double x1, double *Z0, double *Gh, double *Gl, double *A, unsigned *fl, int f32)
 {
     int amb = 0;
     *fl = 0; *A = 0;
     if (isnan(x0)) { *Z0 = NAN; set_exact(NAN, Gh, Gl, fl); return; }
     Q M = expm1f128((Q)x0);
-    *Z0 = rn_double(M, &amb);
+    *Z0 = rn_main(M, &amb, f32);
     if (amb) *fl |= FL_AMBIG;
     if (isnan(x1)) { set_exact(NAN, Gh, Gl, fl); return; }
     if (isinf(*Z0) || (isinf(x0) && x0 < 0)) { set_exact(0.0, Gh, Gl, fl); return; }
@@ -197,14 +240,14 @@ static Q corr_log1p(double y1, Q w, Q base, double Z0, int *special, double *zs)
     return log1pf128(q);
 }
 
-static void ox_log(double y0, double y1, double *Z0, double *Gh, double *Gl, double *A, unsigned *fl)
+static void ox_log(double y0, double y1, double *Z0, double *Gh, double *Gl, double *A, unsigned *fl, int f32)
 {
     int amb = 0, sp = 0;
     double zs = 0;
     *fl = 0; *A = 0;
     if (isnan(y0) || y0 < 0) { *Z0 = NAN; set_exact(NAN, Gh, Gl, fl); return; }
     Q L = logf128((Q)y0);                          /* log(+-0) = -Inf, log(+Inf) = +Inf */
-    *Z0 = rn_double(L, &amb);
+    *Z0 = rn_main(L, &amb, f32);
     if (amb) *fl |= FL_AMBIG;
     if (isnan(y1)) { set_exact(NAN, Gh, Gl, fl); return; }
     if (isinf(*Z0)) { set_exact(0.0, Gh, Gl, fl); return; }
@@ -225,14 +268,14 @@ static void ox_log(double y0, double y1, double *Z0, double *Gh, double *Gl, dou
     *A = (double)qabs(L + P);
 }
 
-static void ox_log1p(double y0, double y1, double *Z0, double *Gh, double *Gl, double *A, unsigned *fl)
+static void ox_log1p(double y0, double y1, double *Z0, double *Gh, double *Gl, double *A, unsigned *fl, int f32)
 {
     int amb = 0, sp = 0;
     double zs = 0;
     *fl = 0; *A = 0;
     if (isnan(y0) || y0 < -1.0) { *Z0 = NAN; set_exact(NAN, Gh, Gl, fl); return; }
     Q L = log1pf128((Q)y0);                        /* log1p(-1) = -Inf */
-    *Z0 = rn_double(L, &amb);
+    *Z0 = rn_main(L, &amb, f32);
     if (amb) *fl |= FL_AMBIG;
     if (isnan(y1)) { set_exact(NAN, Gh, Gl, fl); return; }
     if (isinf(*Z0)) { set_exact(0.0, Gh, Gl, fl); return; }
@@ -334,22 +377,36 @@ void tfo_set_threads(int t)
 #endif
 }
 
+int tfo_eval2(int kind, int f32, int64_t n, const double *x0, const double *x1,
+              const double *y0, const double *y1,
+              double *Z0, double *Gh, double *Gl, double *A, unsigned *flags);
+
 /* Unary: kind in {0 exp, 1 expm1, 2 log, 3 log1p}; x1 may be NULL (dotted argument).
    Binary: kind in {4 add, 5 mul}; x = x0 + x1, y = y0 + y1 (x1, y1 may be NULL). */
 int tfo_eval(int kind, int64_t n, const double *x0, const double *x1,
              const double *y0, const double *y1,
              double *Z0, double *Gh, double *Gl, double *A, unsigned *flags)
 {
-    if (n < 0 || kind < 0 || kind > 5) return -1;
+    return tfo_eval2(kind, 0, n, x0, x1, y0, y1, Z0, Gh, Gl, A, flags);
+}
+
+/* As tfo_eval; f32 = 1 evaluates float twofolds (unary kinds only): the
+   arguments are floats held in doubles, Z0 = f(x0) rounded to float, and
+   G = F - Z0 as before. */
+int tfo_eval2(int kind, int f32, int64_t n, const double *x0, const double *x1,
+              const double *y0, const double *y1,
+              double *Z0, double *Gh, double *Gl, double *A, unsigned *flags)
+{
+    if (n < 0 || kind < 0 || kind > 5 || (f32 && kind >= K_ADD)) return -1;
     if (kind >= K_ADD && !y0) return -1;
 #pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t i = 0; i < n; i++) {
         double a1 = x1 ? x1[i] : 0.0;
         switch (kind) {
-        case K_EXP:   ox_exp(x0[i], a1, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i]); break;
-        case K_EXPM1: ox_expm1(x0[i], a1, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i]); break;
-        case K_LOG:   ox_log(x0[i], a1, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i]); break;
-        case K_LOG1P: ox_log1p(x0[i], a1, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i]); break;
+        case K_EXP:   ox_exp(x0[i], a1, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i], f32); break;
+        case K_EXPM1: ox_expm1(x0[i], a1, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i], f32); break;
+        case K_LOG:   ox_log(x0[i], a1, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i], f32); break;
+        case K_LOG1P: ox_log1p(x0[i], a1, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i], f32); break;
         case K_ADD:   ox_add(x0[i], a1, y0[i], y1 ? y1[i] : 0.0, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i]); break;
         case K_MUL:   ox_mul(x0[i], a1, y0[i], y1 ? y1[i] : 0.0, &Z0[i], &Gh[i], &Gl[i], &A[i], &flags[i]); break;
         }

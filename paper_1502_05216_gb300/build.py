@@ -23,7 +23,7 @@ LIB = os.path.join(LIBDIR, "libtf.so")
 PROBE_LIB = os.path.join(LIBDIR, "libtfprobe.so")
 SOURCES = ["tf_capi.cu", "tf_chain.cu"]
 PROBE_SOURCES = ["tf_probe.cu"]
-HEADERS = ["tf_core.cuh", "tf_eft.cuh", "tf_fixed.cuh", "tf_tables.h", os.path.join(INCLUDE, "tf.h"),
+HEADERS = ["tf_core.cuh", "tf_core_f.cuh", "tf_eft.cuh", "tf_fixed.cuh", "tf_tables.h", os.path.join(INCLUDE, "tf.h"),
            os.path.join(INCLUDE, "tf_probe.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xptxas", "-O3", "--fmad=true",

@@ -8,6 +8,15 @@ All values come from Python's decimal module at 120 significant digits.
       for |N| < 2^19 (argument reduction x = N ln2/256 + r).
   TF_INV_C  256/ln2 rounded to double.
 
+Float twofold (float-float on the FP32 pipes) constants:
+  TF_F_INV_C   256/ln2 rounded to float.
+  TF_F_C0..C2  ln2/256 = C0 + C1 + C2, C0 with 8 significant bits (N*C0 exact
+      for |N| < 2^16), C1, C2 floats (rounded to nearest).
+  TF_F_L0..L2  ln2 = L0 + L1 + L2, L0 with 16 significant bits (n*L0 exact for
+      |n| < 2^8), L1, L2 floats.
+  TF_F_R3..R5  1/3! .. 1/5! rounded to float (the dotted Taylor tail).
+  TF_FT[j], TF_FE[j]  2^(j/256) and 2^(j/256) - 1 as (hi, lo) floats, j = -128 .. 128.
+
 Fixed-point constants of the integer exp core (unsigned integers, rounded to
 nearest, each with its unit):
   TF_TFIX[j]   2^(j/256), units 2^-127, as (lo64, hi64), j = -128 .. 128: the
@@ -31,6 +40,33 @@ import sys
 
 D = decimal.Decimal
 CTX = decimal.Context(prec=120, Emax=99999, Emin=-99999)
+
+
+def f32_nearest(v):
+    """The float nearest to the Decimal v (ties to even), as a Python float."""
+    import numpy as np
+    c = np.float32(float(v))
+    best = None
+    for x in (np.nextafter(c, np.float32(-np.inf)), c, np.nextafter(c, np.float32(np.inf))):
+        d = abs(CTX.subtract(D(float(x)), v))
+        even = (int(np.array(x, dtype=np.float32).view(np.int32)) & 1) == 0
+        key = (d, not even)
+        if best is None or key < best[0]:
+            best = (key, float(x))
+    return best[1]
+
+
+def fsplit_exact(v, n=2):
+    out = []
+    for _ in range(n):
+        h = f32_nearest(v)
+        out.append(h)
+        v = CTX.subtract(v, D(h))
+    return out
+
+
+def hexf(x):
+    return float.hex(x) + "f"
 
 
 def trunc_bits(v, bits):
@@ -58,6 +94,29 @@ def main(out=sys.stdout):
     w(f"#define TF_TAB_HALF 128       /* table index j = -128 .. 128, step ln2/256 */\n")
     w(f"#define TF_INV_C {hexd(inv_c)}  /* 256/ln2 */\n")
     w(f"#define TF_C0 {hexd(C0)}\n")
+    w("\n")
+    # float twofold constants
+    cf = CTX.divide(ln2, 256)
+    FC0 = trunc_bits(cf, 8)
+    FC1, FC2 = fsplit_exact(CTX.subtract(cf, D(FC0)), 2)
+    FL0 = trunc_bits(ln2, 16)
+    FL1, FL2 = fsplit_exact(CTX.subtract(ln2, D(FL0)), 2)
+    w("/* float twofold path */\n")
+    w(f"#define TF_F_TAB_HALF 128\n#define TF_F_INV_C {hexf(f32_nearest(CTX.divide(256, ln2)))}\n")
+    w(f"#define TF_F_C0 {hexf(FC0)}\n#define TF_F_C1 {hexf(FC1)}\n#define TF_F_C2 {hexf(FC2)}\n")
+    w(f"#define TF_F_L0 {hexf(FL0)}\n#define TF_F_L1 {hexf(FL1)}\n#define TF_F_L2 {hexf(FL2)}\n")
+    for m in range(3, 6):
+        w(f"#define TF_F_R{m} {hexf(f32_nearest(CTX.divide(1, D(math.factorial(m)))))}\n")
+    for name, minus1 in (("TF_FT", False), ("TF_FE", True)):
+        w(f"/* {'2^(j/256) - 1' if minus1 else '2^(j/256)'} as (hi, lo) floats; index j + 128 */\n")
+        w(f"TF_TABLE_QUALIFIER float {name}_TABLE[257][2] = {{\n")
+        for j in range(-128, 129):
+            v = CTX.power(D(2), CTX.divide(D(j), 256))
+            if minus1:
+                v = CTX.subtract(v, 1)
+            h, l = fsplit_exact(v, 2)
+            w(f"  {{{hexf(h)}, {hexf(l)}}},\n")
+        w("};\n")
     w("\n")
     def fixed(v, unit_exp):
         """round(v * 2^unit_exp) as a Python int (v a Decimal)."""

@@ -12,6 +12,7 @@
 
 #include "tf.h"
 #include "tf_core.cuh"
+#include "tf_core_f.cuh"
 
 namespace {
 
@@ -42,6 +43,23 @@ struct OpMul {
     __device__ static void eval(double a, double b, double c, double d, double& z0, double& z1) {
         tf::tmul1(a, b, c, d, z0, z1);
     }
+};
+
+struct OpExpF {
+    static constexpr float dummy = 0.0f;
+    __device__ static void eval(float a, float b, float& z0, float& z1) { tff::texpf_impl<true>(a, b, z0, z1); }
+};
+struct OpExpm1F {
+    static constexpr float dummy = 0.0f;
+    __device__ static void eval(float a, float b, float& z0, float& z1) { tff::texpm1f_impl<true>(a, b, z0, z1); }
+};
+struct OpLogF {
+    static constexpr float dummy = 1.0f;
+    __device__ static void eval(float a, float b, float& z0, float& z1) { tff::tlogf_impl<true>(a, b, z0, z1); }
+};
+struct OpLog1pF {
+    static constexpr float dummy = 0.0f;
+    __device__ static void eval(float a, float b, float& z0, float& z1) { tff::tlog1pf_impl<true>(a, b, z0, z1); }
 };
 
 __device__ __forceinline__ double2 ld2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
@@ -92,6 +110,58 @@ __global__ void __launch_bounds__(kThreads) unary_v1(const double* x0, const dou
     double a = in ? x0[i] : Op::dummy;
     double b = (in && x1) ? x1[i] : 0.0;
     double r0, r1;
+    Op::eval(a, b, r0, r1);
+    if (in) {
+        z0[i] = r0;
+        z1[i] = r1;
+    }
+}
+
+// Float twofolds: 4 elements per thread, 128-bit loads and stores.
+template <class Op>
+__global__ void __launch_bounds__(kThreads) unary_f4(const float* __restrict__ x0, const float* __restrict__ x1,
+                                                     float* z0, float* z1, int64_t n) {
+    int64_t i = 4 * ((int64_t)blockIdx.x * kThreads + threadIdx.x);
+    float a[4], b[4], r[4], s[4];
+    bool full = i + 3 < n;
+    if (full) {
+        float4 v = __ldg(reinterpret_cast<const float4*>(x0 + i));
+        a[0] = v.x, a[1] = v.y, a[2] = v.z, a[3] = v.w;
+        float4 w = x1 ? __ldg(reinterpret_cast<const float4*>(x1 + i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        b[0] = w.x, b[1] = w.y, b[2] = w.z, b[3] = w.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            bool in = i + q < n;
+            a[q] = in ? x0[i + q] : Op::dummy;
+            b[q] = (in && x1) ? x1[i + q] : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Op::eval(a[q], b[q], r[q], s[q]);
+    if (full) {
+        __stcs(reinterpret_cast<float4*>(z0 + i), make_float4(r[0], r[1], r[2], r[3]));
+        __stcs(reinterpret_cast<float4*>(z1 + i), make_float4(s[0], s[1], s[2], s[3]));
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (i + q < n) {
+                z0[i + q] = r[q];
+                z1[i + q] = s[q];
+            }
+        }
+    }
+}
+
+// Float twofolds, 1 element per thread, scalar I/O (pointers not 16-byte aligned).
+template <class Op>
+__global__ void __launch_bounds__(kThreads) unary_f1(const float* x0, const float* x1, float* z0, float* z1,
+                                                     int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    bool in = i < n;
+    float a = in ? x0[i] : Op::dummy;
+    float b = (in && x1) ? x1[i] : 0.0f;
+    float r0, r1;
     Op::eval(a, b, r0, r1);
     if (in) {
         z0[i] = r0;
@@ -166,6 +236,25 @@ int run_unary(const double* x0, const double* x1, double* z0, double* z1, int64_
 }
 
 template <class Op>
+int run_unary_f(const float* x0, const float* x1, float* z0, float* z1, int64_t n, void* stream) {
+    if (n < 0 || n > kMaxN) return TF_ERR_SIZE;
+    if (n == 0) return TF_OK;
+    if (!x0 || !z0 || !z1) return TF_ERR_NULL;
+    if (!al(x0, 4) || !al(z0, 4) || !al(z1, 4) || (x1 && !al(x1, 4))) return TF_ERR_ALIGN;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bool vec = al(x0, 16) && al(z0, 16) && al(z1, 16) && (!x1 || al(x1, 16));
+    if (vec) {
+        int64_t threads = (n + 3) / 4;
+        unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
+        unary_f4<Op><<<blocks, kThreads, 0, s>>>(x0, x1, z0, z1, n);
+    } else {
+        unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
+        unary_f1<Op><<<blocks, kThreads, 0, s>>>(x0, x1, z0, z1, n);
+    }
+    return launch_status();
+}
+
+template <class Op>
 int run_binary(const double* x0, const double* x1, const double* y0, const double* y1, double* z0, double* z1,
                int64_t n, void* stream) {
     if (n < 0 || n > kMaxN) return TF_ERR_SIZE;
@@ -211,12 +300,25 @@ int tf_tmul(const double* x0, const double* x1, const double* y0, const double* 
     return run_binary<OpMul>(x0, x1, y0, y1, z0, z1, n, stream);
 }
 
+int tf_texpf(const float* x0, const float* x1, float* z0, float* z1, int64_t n, void* stream) {
+    return run_unary_f<OpExpF>(x0, x1, z0, z1, n, stream);
+}
+int tf_texpm1f(const float* x0, const float* x1, float* z0, float* z1, int64_t n, void* stream) {
+    return run_unary_f<OpExpm1F>(x0, x1, z0, z1, n, stream);
+}
+int tf_tlogf(const float* y0, const float* y1, float* z0, float* z1, int64_t n, void* stream) {
+    return run_unary_f<OpLogF>(y0, y1, z0, z1, n, stream);
+}
+int tf_tlog1pf(const float* y0, const float* y1, float* z0, float* z1, int64_t n, void* stream) {
+    return run_unary_f<OpLog1pF>(y0, y1, z0, z1, n, stream);
+}
+
 const char* tf_strerror(int code) {
     switch (code) {
         case TF_OK: return "ok";
         case TF_ERR_NULL: return "a required pointer is NULL";
         case TF_ERR_SIZE: return "n is negative or too large";
-        case TF_ERR_ALIGN: return "a pointer is not 8-byte aligned";
+        case TF_ERR_ALIGN: return "a pointer is not aligned to its element size";
         case TF_ERR_LAUNCH: return "kernel launch failed";
         case TF_ERR_NODEVICE: return "no usable CUDA device";
         case TF_ERR_ARG: return "invalid argument";

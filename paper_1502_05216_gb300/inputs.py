@@ -303,3 +303,88 @@ def _uniform_at(seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
     base = np.uint64((seed << 40) | (stream << 36))
     c = idx.astype(np.uint64) + base
     return (splitmix64(c) >> np.uint64(11)).astype(np.float64) * 2.0**-53
+
+
+# ---------------------------------------------------------------------------------
+# Float twofolds (the precision tier): float arguments, x1 = RN_f(x0 u 2^-24).
+# ---------------------------------------------------------------------------------
+
+EXPF_OVERFLOW = 88.72283935546875      # e^x rounds to +Inf in float from about here
+EXPF_UNDERFLOW = -103.97207708          # e^x rounds to 0 in float below about here
+EXPF_SUBNORMAL = -87.33654475           # e^x < 2^-126 below this
+
+SPECIALS_F = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1.0, -1.0, 2.0**-149, -2.0**-149,
+                       2.0**-126, 3.4028234663852886e38, -3.4028234663852886e38], dtype=np.float32)
+
+
+def _f32(x):
+    with np.errstate(over="ignore"):
+        return np.asarray(x, dtype=np.float64).astype(np.float32)
+
+
+def _perturb_f32(x0, seed, n, start):
+    u = 2.0 * uniform(seed, S_PERT, n, start) - 1.0
+    with np.errstate(invalid="ignore", over="ignore"):
+        return _f32(x0.astype(np.float64) * u * 2.0**-24)
+
+
+def workload_f32(func: str, n: int, start: int = 0):
+    """(x0, x1) float32 arrays of a unary function's float workload:
+      texp   x0 uniform in [-88, 88] (the double texp workload within float range)
+      texpm1 random sign, |x0| log-uniform in [2^-40, 88]
+      tlog   x0 log-uniform in [2^-126, 2^127]
+      tlog1p half random sign |x0| log-uniform in [2^-40, 2^-10), half x0 = t - 1,
+             t log-uniform in [2^-24, 2^100]
+    and x1 = RN_f(x0 u 2^-24), u uniform in [-1, 1]."""
+    seed = {"texp": 6, "texpm1": 16, "tlog": 7, "tlog1p": 17}[func]
+    if func == "texp":
+        x0 = _f32(-88.0 + 176.0 * uniform(seed, S_MAG, n, start))
+    elif func == "texpm1":
+        x0 = _f32(_signs(seed, n, start) * _loguniform(-40.0, math.log2(88.0), seed, n, start))
+    elif func == "tlog":
+        x0 = _f32(_loguniform(-126.0, 127.0, seed, n, start))
+    else:
+        pick = uniform(seed, S_PICK, n, start) < 0.5
+        small = _signs(seed, n, start) * _loguniform(-40.0, -10.0, seed, n, start)
+        t = _loguniform(-24.0, 100.0, seed, n, start)
+        x0 = _f32(np.where(pick, small, t - 1.0))
+    return x0, _perturb_f32(x0, seed, n, start)
+
+
+def _half_ulp_f32(x0):
+    with np.errstate(invalid="ignore", over="ignore"):
+        a = np.abs(x0.astype(np.float32))
+        return ((np.nextafter(a, np.float32(np.inf)) - a) * np.float32(0.5)).astype(np.float32)
+
+
+def hard_cases_f32(func: str, n: int, seed: int = 19, start: int = 0):
+    """Float hard cases: thresholds of overflow/subnormal/underflow, tiny
+    arguments, log near 1 and of subnormals, log1p near -1; x1 = 0 (10%),
+    exactly +-half an ulp (5%), the IEEE specials paired at the end."""
+    U = lambda s: uniform(seed, s, n, start)  # noqa: E731
+    w = 2.0**-6
+    if func in ("texp", "texpm1"):
+        parts = [EXPF_OVERFLOW + w * (2 * U(5) - 1), EXPF_UNDERFLOW + w * (2 * U(6) - 1),
+                 EXPF_SUBNORMAL + w * (2 * U(7) - 1),
+                 EXPF_UNDERFLOW + (EXPF_SUBNORMAL - EXPF_UNDERFLOW) * U(8),
+                 _signs(seed, n, start) * np.exp2(-149 + 140 * U(9)),
+                 -(np.exp2(3.0 + 4.0 * U(10)))]
+    elif func == "tlog":
+        parts = [1.0 + _signs(seed, n, start) * np.exp2(-24 + 20 * U(5)), np.exp2(-149 + 23 * U(6)),
+                 np.exp2(100 + 28 * U(7)), np.exp2(-126 + 253 * U(8))]
+    else:
+        parts = [-1.0 + np.exp2(-24 + 22 * U(5)), _signs(seed, n, start) * np.exp2(-149 + 140 * U(6)),
+                 np.exp2(60 + 68 * U(7)), -0.5 + 0.25 * U(8)]
+    k = -(-n // len(parts))
+    x0 = _f32(np.concatenate([np.asarray(p)[:k] for p in parts])[:n])
+    x1 = _perturb_f32(x0, seed, n, start)
+    pick = U(4)
+    sgn = np.where(U(1) < 0.5, -1.0, 1.0).astype(np.float32)
+    x1 = np.where(pick < 0.10, np.float32(0.0), x1).astype(np.float32)
+    x1 = np.where((pick >= 0.10) & (pick < 0.15), sgn * _half_ulp_f32(x0), x1).astype(np.float32)
+    m = SPECIALS_F.shape[0]
+    k = min(n, m * m)
+    if k:
+        x0[n - k:] = np.repeat(SPECIALS_F, m)[:k]
+        x1[n - k:] = (np.tile(SPECIALS_F, m)[:k].astype(np.float64) * 2.0**-30).astype(np.float32)
+    return x0, x1

@@ -43,6 +43,10 @@ def load(path: str | None = None):
             f = getattr(lib, "tf_" + name)
             f.argtypes = [vp, vp, vp, vp, i64, vp]
             f.restype = i32
+        for name in UNARY:
+            f = getattr(lib, "tf_" + name + "f")
+            f.argtypes = [vp, vp, vp, vp, i64, vp]
+            f.restype = i32
         for name in BINARY:
             f = getattr(lib, "tf_" + name)
             f.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
@@ -66,14 +70,15 @@ def _check(rc: int, name: str):
         raise TwofoldError(f"tf_{name}: {load().tf_strerror(rc).decode()} (code {rc})")
 
 
-def _ptr(t, name, n, device):
+def _ptr(t, name, n, device, dtype=None):
     import torch
     if t is None:
         return None
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
-    if t.dtype != torch.float64 or not t.is_cuda or t.device != device:
-        raise TypeError(f"{name} must be a float64 CUDA tensor on {device}")
+    dtype = dtype or torch.float64
+    if t.dtype != dtype or not t.is_cuda or t.device != device:
+        raise TypeError(f"{name} must be a {dtype} CUDA tensor on {device}")
     if not t.is_contiguous() or t.numel() != n:
         raise ValueError(f"{name} must be contiguous with {n} elements")
     return t.data_ptr()
@@ -94,6 +99,19 @@ def _unary(name, x0, x1=None, out=None, stream=None):
     args = (_ptr(x0, "x0", n, dev), _ptr(x1, "x1", n, dev), _ptr(out[0], "z0", n, dev),
             _ptr(out[1], "z1", n, dev))
     _check(getattr(load(), "tf_" + name)(*args, n, _stream(stream, dev)), name)
+    return out
+
+
+def _unary_f(name, x0, x1=None, out=None, stream=None):
+    import torch
+    n = x0.numel()
+    dev = x0.device
+    if out is None:
+        out = (torch.empty_like(x0), torch.empty_like(x0))
+    f32 = torch.float32
+    args = (_ptr(x0, "x0", n, dev, f32), _ptr(x1, "x1", n, dev, f32), _ptr(out[0], "z0", n, dev, f32),
+            _ptr(out[1], "z1", n, dev, f32))
+    _check(getattr(load(), "tf_" + name + "f")(*args, n, _stream(stream, dev)), name + "f")
     return out
 
 
@@ -137,6 +155,29 @@ def tadd(x0, x1, y0, y1, out=None, stream=None):
 def tmul(x0, x1, y0, y1, out=None, stream=None):
     """(z0, z1) with z0 = x0 * y0 (plain) and z0 + z1 = (x0 + x1)(y0 + y1)."""
     return _binary("tmul", x0, x1, y0, y1, out, stream)
+
+
+def texpf(x0, x1=None, out=None, stream=None):
+    """Float twofolds: (z0, z1) float32 with z0 + z1 = e^(x0 + x1), z0 = RN_f(e^x0)."""
+    return _unary_f("texp", x0, x1, out, stream)
+
+
+def texpm1f(x0, x1=None, out=None, stream=None):
+    """Float twofolds: z0 + z1 = e^(x0 + x1) - 1."""
+    return _unary_f("texpm1", x0, x1, out, stream)
+
+
+def tlogf(y0, y1=None, out=None, stream=None):
+    """Float twofolds: z0 + z1 = log(y0 + y1)."""
+    return _unary_f("tlog", y0, y1, out, stream)
+
+
+def tlog1pf(y0, y1=None, out=None, stream=None):
+    """Float twofolds: z0 + z1 = log(1 + y0 + y1)."""
+    return _unary_f("tlog1p", y0, y1, out, stream)
+
+
+FUNCS_F = {"texp": texpf, "texpm1": texpm1f, "tlog": tlogf, "tlog1p": tlog1pf}
 
 
 # operation codes of the chain entry points (TF_OP_* in include/tf.h)

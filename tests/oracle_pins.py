@@ -334,6 +334,59 @@ def pin_cancellation(lib):
     return fails
 
 
+def mainpart_points_f32():
+    """Float arguments per function: the float workloads plus the thresholds."""
+    n = 120
+    pts = {}
+    for func in UNARY:
+        pts[func] = [I.workload_f32(func, n, start=500)[0], I.hard_cases_f32(func, 100, seed=150)[0][:90]]
+    pts["texp"].append(np.float32([88.72283, 88.72284, -103.97207, -103.97208, -87.33654, 0.0, 1.0]))
+    pts["tlog"].append(np.float32([1.0, 2.0, 0.5, 1.0000001, 0.99999994, 2.0**-149, 3.4028235e38]))
+    pts["tlog1p"].append(np.float32([-0.99999994, 1e-30, -1e-30, 1.0, 3.4028235e38]))
+    pts["texpm1"].append(np.float32([1e-30, -1e-30, -88.0, 88.7, 0.3465736]))
+    out = {}
+    for func, parts in pts.items():
+        x = np.concatenate(parts).astype(np.float64)
+        out[func] = x[np.isfinite(x)]
+    return out
+
+
+@_hiprec
+def pin_mainpart_decimal_f32(lib):
+    """Float twofolds: Z0 equals the decimal value rounded to the nearest float."""
+    fails = []
+    for func, x0 in mainpart_points_f32().items():
+        r = oracle.evaluate(func, x0, None, lib=lib, dtype="f32")
+        for i, x in enumerate(x0):
+            if func == "tlog" and x < 0 or func == "tlog1p" and x < -1:
+                continue
+            want = oracle.round_to_float(dec_eval(func, _D(x)))
+            if not (r.Z0[i] == want or (math.isnan(want) and math.isnan(r.Z0[i]))):
+                fails.append(f"{func}f({x!r}): Z0={r.Z0[i]!r} decimal={want!r}")
+    return fails
+
+
+@_hiprec
+def pin_deviation_decimal_f32(lib):
+    """Float twofolds: Gh + Gl equals F - Z0, F = f(x0 + x1) in decimal."""
+    fails = []
+    c = _ctx(80)
+    for func, x0 in mainpart_points_f32().items():
+        x1 = (x0 * (2 * _u(160, x0.shape[0]) - 1) * 2.0**-24).astype(np.float32).astype(np.float64)
+        r = oracle.evaluate(func, x0, x1, lib=lib, dtype="f32")
+        for i in range(x0.shape[0]):
+            if r.flags[i] & oracle.FL_EXACT:
+                continue
+            d = c.add(_D(x0[i]), _D(x1[i]))
+            if func == "tlog" and d <= 0 or func == "tlog1p" and d <= -1:
+                continue
+            F = dec_eval(func, d, 70)
+            G = c.subtract(F, _D(r.Z0[i]))
+            if not _close(r.Gh[i], r.Gl[i], G, F):
+                fails.append(f"{func}f({x0[i]!r}+{x1[i]!r}): G={r.Gh[i]!r}+{r.Gl[i]!r} decimal={G:.6e}")
+    return fails
+
+
 def _chain_batch(ops_list, a_list, s_init):
     """A step-major batch (include/tf.h layout) from per-chain lists of op codes,
     operands (a0, a1) and initial states (s0, s1); chains must be given
@@ -408,4 +461,4 @@ def pin_chain_condition(lib):
 
 ALL_PINS = [pin_mainpart_decimal, pin_deviation_decimal, pin_closed_forms, pin_series,
             pin_invariants, pin_special, pin_arith, pin_cancellation, pin_chain_decimal,
-            pin_chain_condition]
+            pin_chain_condition, pin_mainpart_decimal_f32, pin_deviation_decimal_f32]

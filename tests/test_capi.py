@@ -25,7 +25,8 @@ def lib():
 
 def test_header_declares_the_entry_points():
     names = declared()
-    for f in ("tf_texp", "tf_texpm1", "tf_tlog", "tf_tlog1p", "tf_tadd", "tf_tmul", "tf_strerror"):
+    for f in ("tf_texp", "tf_texpm1", "tf_tlog", "tf_tlog1p", "tf_tadd", "tf_tmul", "tf_strerror",
+              "tf_texpf", "tf_texpm1f", "tf_tlogf", "tf_tlog1pf", "tf_chain", "tf_chain_step"):
         assert f in names
 
 
@@ -52,6 +53,14 @@ def test_error_codes_before_any_launch(lib):
         assert f(good, good, good, None, 5, None) == 1
         assert f(odd, good, good, good, 5, None) == 3                  # TF_ERR_ALIGN
         assert f(good, odd, good, good, 5, None) == 3
+    odd2 = ctypes.c_void_p((1 << 20) + 2)  # not 4-byte aligned
+    for name in ("tf_texpf", "tf_texpm1f", "tf_tlogf", "tf_tlog1pf"):
+        f = getattr(lib, name)
+        assert f(good, good, good, good, 0, None) == 0
+        assert f(good, good, good, good, -1, None) == 2
+        assert f(None, good, good, good, 5, None) == 1
+        assert f(odd2, good, good, good, 5, None) == 3
+        assert f(good, good, good, odd2, 5, None) == 3
     for name in ("tf_tadd", "tf_tmul"):
         f = getattr(lib, name)
         assert f(good, good, good, good, good, good, 0, None) == 0

@@ -1,0 +1,117 @@
+"""Parity of the float-twofold kernels (tf_texpf, tf_texpm1f, tf_tlogf,
+tf_tlog1pf) with the CPU oracle in float mode.
+
+Same bar as the double path, at float precision: z0 equals f(x0) correctly
+rounded to float in >= 99.999% of the elements and is never more than 1 float
+ulp away; z0 + z1 is within 2^-44 |F| + 2^-23 |G| + 2^-149 of f(x0 + x1)
+(tests/tfcheck.py); special-value z1 bitwise.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import tfcheck
+from paper_1502_05216_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+UNARY = ("texp", "texpm1", "tlog", "tlog1p")
+
+
+@pytest.fixture(scope="module")
+def tf():
+    import torch
+    from paper_1502_05216_gb300 import build, tf as tfmod
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test collected on a machine without CUDA")
+    build.build()
+    tfmod.load()
+    return tfmod
+
+
+def run(tf, func, x0, x1):
+    import torch
+    d = [None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda() for a in (x0, x1)]
+    z0, z1 = tf.FUNCS_F[func](*d)
+    torch.cuda.synchronize()
+    return z0.cpu().numpy(), z1.cpu().numpy()
+
+
+def check(tf, func, x0, x1, where, rate=0.99999):
+    z0, z1 = run(tf, func, x0, x1)
+    orc = oracle.evaluate(func, x0.astype(np.float64), None if x1 is None else x1.astype(np.float64),
+                          dtype="f32")
+    return tfcheck.check(z0.astype(np.float64), z1.astype(np.float64), orc, "f32", rate, where)
+
+
+@pytest.mark.parametrize("func", UNARY)
+def test_workload_parity_f32(tf, func):
+    st = check(tf, func, *I.workload_f32(func, 2**17 + 37), f"{func}f workload")
+    print(func, st)
+
+
+@pytest.mark.parametrize("func", UNARY)
+def test_hard_cases_f32(tf, func):
+    st = check(tf, func, *I.hard_cases_f32(func, 2**16), f"{func}f hard cases")
+    print(func, st)
+
+
+@pytest.mark.parametrize("func", UNARY)
+def test_special_values_f32(tf, func):
+    s = I.SPECIALS_F
+    x0 = np.repeat(s, s.shape[0])
+    x1 = np.tile(s, s.shape[0])
+    check(tf, func, x0, x1, f"{func}f specials", rate=1.0)
+
+
+@pytest.mark.parametrize("func", UNARY)
+def test_dotted_f32(tf, func):
+    x0, x1 = I.workload_f32(func, 2**14 + 3)
+    z0, _ = run(tf, func, x0, None)
+    check(tf, func, x0, None, f"{func}f dotted")
+    w0, _ = run(tf, func, x0, x1)
+    assert np.array_equal(z0.view(np.int32), w0.view(np.int32))  # main part depends on x0 only
+
+
+@pytest.mark.parametrize("func", UNARY)
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 127, 1025])
+def test_small_sizes_f32(tf, func, n):
+    check(tf, func, *I.workload_f32(func, n, start=77), f"{func}f n={n}")
+
+
+@pytest.mark.parametrize("func", UNARY)
+def test_misaligned_equals_aligned_f32(tf, func):
+    """Pointers 4- but not 16-byte aligned take the scalar kernel: same bits."""
+    import torch
+    n = 4099
+    x0, x1 = I.workload_f32(func, n)
+    ref = run(tf, func, x0, x1)
+    bufs = []
+    for a in (x0, x1):
+        b = torch.zeros(n + 1, dtype=torch.float32, device="cuda:0")
+        b[1:] = torch.from_numpy(a).cuda()
+        bufs.append(b[1:])
+    o0 = torch.zeros(n + 1, dtype=torch.float32, device="cuda:0")
+    o1 = torch.zeros(n + 1, dtype=torch.float32, device="cuda:0")
+    tf.FUNCS_F[func](bufs[0], bufs[1], out=(o0[1:], o1[1:]))
+    torch.cuda.synchronize()
+    assert np.array_equal(o0[1:].cpu().numpy().view(np.int32), ref[0].view(np.int32))
+    assert np.array_equal(o1[1:].cpu().numpy().view(np.int32), ref[1].view(np.int32))
+
+
+@pytest.mark.parametrize("func", ("texp", "tlog"))
+def test_full_size_sampled_f32(tf, func):
+    """n = 2^28 floats (the precision-tier size), every 2^11-th element and the
+    ragged tail checked against the oracle."""
+    import torch
+    n = 2**28
+    x0, x1 = I.workload_f32(func, n)
+    d0, d1 = torch.from_numpy(x0).cuda(), torch.from_numpy(x1).cuda()
+    z0, z1 = tf.FUNCS_F[func](d0, d1)
+    torch.cuda.synchronize()
+    idx = np.concatenate([np.arange(0, n, 2**11), np.arange(n - 1000, n)])
+    ti = torch.from_numpy(idx).cuda()
+    h0, h1 = z0[ti].cpu().numpy(), z1[ti].cpu().numpy()
+    orc = oracle.evaluate(func, x0[idx].astype(np.float64), x1[idx].astype(np.float64), dtype="f32")
+    st = tfcheck.check(h0.astype(np.float64), h1.astype(np.float64), orc, "f32", 0.99999, f"{func}f 2^28 sampled")
+    print(func, st)

@@ -9,7 +9,7 @@ PLANTS = {1: "texp drops the x1 term", 2: "tlog correction has the wrong sign",
           3: "tlog1p correction uses the wrong base", 4: "main part rounded toward zero",
           5: "tmul drops a cross term", 6: "tadd error term with transposed operands",
           7: "texp rounds x0 + x1 to double first", 8: "chain product drops the operand tail",
-          9: "chain condition sum ignores the gains"}
+          9: "chain condition sum ignores the gains", 10: "float main part rounded toward zero"}
 
 
 @pytest.mark.parametrize("k", sorted(PLANTS), ids=lambda k: PLANTS[k].replace(" ", "_"))
