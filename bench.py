@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-chains", action="store_true", help="skip the batched-chains measurement")
+    ap.add_argument("--no-tier", action="store_true", help="skip the float/double precision-tier measurement")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the size sweep")
+    ap.add_argument("--tier-log2n", type=int, default=28)
     ap.add_argument("--funcs", default=",".join(FUNCS),
                     help="comma-separated subset (for profiling a single kernel)")
     return ap.parse_args()
@@ -233,6 +236,85 @@ def chains_bench(dev):
             "tuning": [[r["threads"], r["blocks"], round(r["ms"], 3)] for r in table]}
 
 
+def _time_launches(fn, reps=5, warm=3):
+    """Median ms of one call of fn() (CUDA events on the current stream)."""
+    import torch
+    st = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def precision_tier(dev, log2n):
+    """texp and tlog over float twofolds (float-float on the FP32 pipes) and
+    over double twofolds (the FP64 + integer path) on the same x0 values, n =
+    2^log2n each; Gelem/s and HBM GB/s of each kernel."""
+    import torch
+    from paper_1502_05216_gb300 import inputs as I, tf
+    n = 1 << log2n
+    out = {"n": n, "workload": "texp x0 uniform in [-88, 88]; tlog x0 log-uniform in [2^-126, 2^127]; "
+                               "x1 = x0 u 2^-24 (float) or 2^-53 (double), same x0 and u"}
+    for func in ("texp", "tlog"):
+        x0f, x1f = I.workload_f32_big(func, n)
+        x0d, x1d = I.double_of_f32(func, x0f)
+        res = {}
+        for dt, (a0, a1), fn, bpe in (("f32", (x0f, x1f), tf.FUNCS_F[func], 16),
+                                      ("f64", (x0d, x1d), tf.FUNCS[func], 32)):
+            d0, d1 = torch.from_numpy(a0).to(dev), torch.from_numpy(a1).to(dev)
+            o = (torch.empty_like(d0), torch.empty_like(d0))
+            ms = _time_launches(lambda: fn(d0, d1, out=o))
+            res[dt] = {"ms": ms, "gelem_s": n / (ms * 1e-3) / 1e9, "hbm_gbs": bpe * n / (ms * 1e-3) / 1e9,
+                       "hbm_frac": bpe * n / (ms * 1e-3) / 1e9 / 6804.4}
+            del d0, d1, o
+        res["f32_over_f64"] = res["f64"]["ms"] / res["f32"]["ms"]
+        out[func] = res
+        del x0f, x1f, x0d, x1d
+    torch.cuda.empty_cache()
+    return out
+
+
+def size_sweep(dev, dargs):
+    """texp and tlog (double) at n = 2^10 .. 2^26 (prefixes of the resident
+    2^26 inputs); up to 2^18 the timed unit is a CUDA graph of 64 launches, so
+    the host launch cost is out of the per-launch time."""
+    import torch
+    from paper_1502_05216_gb300 import tf
+    out = {}
+    for func in ("texp", "tlog"):
+        rows = []
+        for lg in (10, 14, 18, 22, 26):
+            n = 1 << lg
+            a0, a1 = dargs[func][0][:n], dargs[func][1][:n]
+            o = (torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.float64, device=dev))
+            if lg <= 18:
+                reps = 64
+                s = torch.cuda.Stream(dev)
+                s.wait_stream(torch.cuda.current_stream(dev))
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.stream(s):
+                    tf.FUNCS[func](a0, a1, out=o, stream=s)
+                    s.synchronize()
+                    with torch.cuda.graph(g, stream=s):
+                        for _ in range(reps):
+                            tf.FUNCS[func](a0, a1, out=o, stream=s)
+                torch.cuda.current_stream(dev).wait_stream(s)
+                ms = _time_launches(g.replay) / reps
+            else:
+                ms = _time_launches(lambda: tf.FUNCS[func](a0, a1, out=o))
+            rows.append({"n": n, "us": ms * 1e3, "gelem_s": n / (ms * 1e-3) / 1e9, "graph": lg <= 18})
+        out[func] = rows
+    return out
+
+
 def ours(a, world, rank, local):
     global FUNCS
     FUNCS = tuple(f for f in a.funcs.split(",") if f)
@@ -340,6 +422,8 @@ def ours(a, world, rank, local):
                "fp64_frac": FP64_PER_ELEM[f] * n / (kern_ms[f] * 1e-3) / peak,
                "hbm_gbs": BYTES_PER_ELEM[f] * n / (kern_ms[f] * 1e-3) / 1e9} for f in FUNCS}
     chain = None if a.no_chains else chains_bench(dev)
+    sweep = None if (a.no_sweep or a.log2n < 26 or "texp" not in dargs or "tlog" not in dargs) else size_sweep(dev, dargs)
+    tier = None if a.no_tier else precision_tier(dev, a.tier_log2n)
     cpu = None
     if world == 1 and not a.no_cpu_baseline:
         rate, cores, sample, _, _ = oracle_rate(12.0)
@@ -351,7 +435,8 @@ def ours(a, world, rank, local):
         "config": {"workload": WORKLOAD, "n": n, "functions": list(FUNCS),
                    "l2": "no flush: every input array (512 MiB) is larger than L2", "parallelism": f"dp{world}"},
         "roofline": roof, "per_func": per, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": len(FUNCS) * a.steps, "clocks": ck, "chains": chain,
+        "gpu_launches": len(FUNCS) * a.steps, "clocks": ck, "chains": chain, "precision_tier": tier,
+        "size_sweep": sweep,
     }), flush=True)
 
 

@@ -351,6 +351,27 @@ def workload_f32(func: str, n: int, start: int = 0):
     return x0, _perturb_f32(x0, seed, n, start)
 
 
+def workload_f32_big(func: str, n: int, start: int = 0, chunk: int = 1 << 21):
+    """workload_f32 for large n, drawn in chunks on a thread pool (each element
+    depends on its index only, so the values are those of workload_f32)."""
+    if n <= chunk:
+        return workload_f32(func, n, start)
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+    pieces = [(s, min(chunk, n - s)) for s in range(0, n, chunk)]
+    with ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+        parts = list(ex.map(lambda p: workload_f32(func, p[1], start + p[0]), pieces))
+    return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
+
+
+def double_of_f32(func: str, x0f: np.ndarray, start: int = 0):
+    """The double twofold over the same x0 values as a float workload (the
+    precision-tier comparison): x0 exactly, x1 = RN(x0 u 2^-53) with the same u."""
+    seed = {"texp": 6, "texpm1": 16, "tlog": 7, "tlog1p": 17}[func]
+    x0 = x0f.astype(np.float64)
+    return x0, _perturb(x0, seed, x0.shape[0], start, 53)
+
+
 def _half_ulp_f32(x0):
     with np.errstate(invalid="ignore", over="ignore"):
         a = np.abs(x0.astype(np.float32))

@@ -115,3 +115,23 @@ def test_full_size_sampled_f32(tf, func):
     orc = oracle.evaluate(func, x0[idx].astype(np.float64), x1[idx].astype(np.float64), dtype="f32")
     st = tfcheck.check(h0.astype(np.float64), h1.astype(np.float64), orc, "f32", 0.99999, f"{func}f 2^28 sampled")
     print(func, st)
+
+
+@pytest.mark.parametrize("func", UNARY)
+def test_precision_tier_same_x0(tf, func):
+    """The precision tier: each function over float twofolds and over double
+    twofolds on the same x0 values (x1 = x0 u 2^-24 and x0 u 2^-53, same u),
+    each checked against the oracle at its own precision; prints both error
+    statistics side by side."""
+    import torch
+    n = 2**16
+    x0f, x1f = I.workload_f32(func, n, start=3 << 20)
+    x0d, x1d = I.double_of_f32(func, x0f, start=3 << 20)
+    stf = check(tf, func, x0f, x1f, f"{func}f tier")
+    d = [torch.from_numpy(a).cuda() for a in (x0d, x1d)]
+    z0, z1 = tf.FUNCS[func](*d)
+    torch.cuda.synchronize()
+    orc = oracle.evaluate(func, x0d, x1d)
+    std = tfcheck.check(z0.cpu().numpy(), z1.cpu().numpy(), orc, "f64", 0.99999, f"{func} tier", func, (x0d, x1d))
+    print(f"tier {func}: f32 max 2^{stf['max_rel_log2']:.1f} mean 2^{stf['mean_rel_log2']:.1f} | "
+          f"f64 max 2^{std['max_rel_log2']:.1f} mean 2^{std['mean_rel_log2']:.1f}")
