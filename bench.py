@@ -75,6 +75,24 @@ def parse():
     return ap.parse_args()
 
 
+def rank_start(rank: int, n: int) -> int:
+    """First element index of a rank's shard: weak scaling, each rank evaluates
+    its own n consecutive elements of every workload (elements are independent,
+    so no data-path collective is needed)."""
+    return rank * n
+
+
+def reduce_max(value: float, world: int, device) -> float:
+    """The maximum of a per-rank value over all ranks (timings: the job takes as
+    long as its slowest rank).  One all_reduce on the initialised process group."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -328,7 +346,7 @@ def ours(a, world, rank, local):
     build.build()
     tf.load()
     n = 1 << a.log2n
-    start = rank * n  # weak scaling: each rank evaluates its own n elements
+    start = rank_start(rank, n)
 
     host = {f: I.workload(f, n, start=start) for f in FUNCS}
     dargs = {f: [torch.from_numpy(x).to(dev) for x in host[f]] for f in FUNCS}
@@ -371,10 +389,7 @@ def ours(a, world, rank, local):
     ck = clocks.stop()
     ms = t0.elapsed_time(t1) / a.steps
     kern_ms = {f: statistics.mean(e[f][0].elapsed_time(e[f][1]) for e in evs) for f in FUNCS}
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, world, dev)
     elems = world * n * len(FUNCS)
     value = elems / (ms * 1e-3) / 1e9
 
@@ -395,10 +410,7 @@ def ours(a, world, rank, local):
                 pipe.run(f, *pin[f], out=out)
         barrier()
         dt = (time.perf_counter() - c0) / ke
-        if world > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = reduce_max(dt, world, dev)
         h2d = sum(8 * n * len(host[f]) for f in FUNCS)
         e2e = {"value": elems / dt / 1e9, "unit": "Gelem/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 16 * n * len(FUNCS), "ms_per_step": dt * 1e3,
