@@ -421,10 +421,13 @@ __device__ __forceinline__ float add_log1p_ratio(float q, float S0, float c) {
     return add(q, fma_rn(q, S0, cc));
 }
 
-// |y1| > 2^-24 |ref| (or y1 not finite): not coupled.
+// |y1| > 2^-24 |ref| (or y1 not finite): not coupled.  For |ref| < 2^-102 the
+// threshold is the significand shifted into the subnormal range.
 __device__ __forceinline__ bool loose(float y1, float ref) {
     uint32_t ar = absbits(ref);
-    uint32_t thr = (ar > (24u << 23)) ? ar - (24u << 23) : 0u;
+    int e = (int)(ar >> 23);
+    uint32_t m = (ar & kMantMask) | (e ? (1u << 23) : 0u);
+    uint32_t thr = (e > 24) ? ar - (24u << 23) : (m >> (25 - max(e, 1)));
     return absbits(y1) > thr;
 }
 
