@@ -42,7 +42,7 @@ WORKLOAD = ("texp, texpm1, tlog, tlog1p (+ tadd, tmul) over double twofolds, n=2
 # _pred_on.sum.per_cycle_elapsed x sm__cycles_elapsed.avg / n, from one
 # --set full capture at n = 2^25 (profiles/unary_v2_intcore_n2p25.md); tadd/tmul
 # are counted from the source (5 each).
-FP64_PER_ELEM = {"texp": 10.0, "texpm1": 12.0, "tlog": 26.5, "tlog1p": 31.9, "tadd": 5.0, "tmul": 5.0}
+FP64_PER_ELEM = {"texp": 10.0, "texpm1": 12.0, "tlog": 26.0, "tlog1p": 33.0, "tadd": 5.0, "tmul": 5.0}
 FP64_COUNT_SOURCE = "ncu SASS counters (unary kernels), source count (tadd/tmul)"
 # HBM bytes per element: SoA doubles in + out.
 BYTES_PER_ELEM = {"texp": 32, "texpm1": 32, "tlog": 32, "tlog1p": 32, "tadd": 48, "tmul": 48}
@@ -50,12 +50,12 @@ BYTES_PER_ELEM = {"texp": 32, "texpm1": 32, "tlog": 32, "tlog1p": 32, "tadd": 48
 # same capture at n = 2^25, scaled by 2 to the benchmark's n = 2^26 (the traffic
 # of an elementwise kernel is proportional to n).  The writes still held in L2 when
 # a launch ends are not in its count.
-TRAFFIC_PER_LAUNCH = {"texp": 2.0483e9, "texpm1": 2.0461e9, "tlog": 2.0457e9, "tlog1p": 2.0490e9}
+TRAFFIC_PER_LAUNCH = {"texp": 2.0472e9, "texpm1": 2.0459e9, "tlog": 2.0491e9, "tlog1p": 2.0492e9}
 TRAFFIC_N = 1 << 26
 # Pipe utilisation of the same capture (sm__inst_executed_pipe_{fp64,alu}, % of
 # peak while active): the kernels are co-limited by the FP64 and integer pipes.
 PIPES = {"texp": {"fp64_pct": 55.6, "alu_pct": 78.3}, "texpm1": {"fp64_pct": 60.4, "alu_pct": 80.5},
-         "tlog": {"fp64_pct": 56.5, "alu_pct": 56.0}, "tlog1p": {"fp64_pct": 60.4, "alu_pct": 53.8}}
+         "tlog": {"fp64_pct": 65.4, "alu_pct": 77.5}, "tlog1p": {"fp64_pct": 73.6, "alu_pct": 73.0}}
 
 def parse():
     ap = argparse.ArgumentParser()
