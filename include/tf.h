@@ -14,6 +14,9 @@
  *     doubles of length n.
  *   - Ownership: every pointer is a DEVICE pointer owned by the caller; the
  *     library allocates and frees nothing and keeps no pointer after the call.
+ *     Pinned host memory (cudaHostAlloc / cudaHostRegister) is addressable from
+ *     the device under unified addressing and may be passed as well: the
+ *     kernel then reads and writes host memory over the GPU's host link.
  *   - x1 (and y1 for the binary operations) may be NULL: the argument is then
  *     "dotted", x1 = 0 (the paper's texp0/texpm10/tlog0/tlog1p0 variants).
  *     x0, z0 and z1 must not be NULL when n > 0.

@@ -303,12 +303,48 @@ class HostPipeline:
 _pipes = {}
 
 
-def call_host(name, *host_arrays, out=None, device="cuda"):
-    """End-to-end call on host arrays (numpy or CPU torch tensors, pinned for
-    speed): copy in, run the kernel, copy (z0, z1) back, pipelined over chunks
+def _pinned_ptr(t, name, n):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or not t.is_pinned():
+        raise TypeError(f"{name} must be a pinned float64 CPU tensor for the zero-copy call")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return t.data_ptr()
+
+
+def call_host_zero_copy(name, *host_arrays, out=None, device="cuda", stream=None):
+    """End-to-end call on pinned host arrays without staging copies: the kernel
+    itself loads the arguments from pinned host memory and stores (z0, z1)
+    there, over the GPU's link to host memory (pinned host memory is
+    addressable from the device under unified addressing).  Returns ``out``
+    after the kernel has finished."""
+    import torch
+    dev = torch.device(device)
+    h = list(host_arrays)
+    n = h[0].numel()
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float64, pin_memory=True),
+               torch.empty(n, dtype=torch.float64, pin_memory=True))
+    names = ("x0", "x1") if len(h) == 2 else ("x0", "x1", "y0", "y1")
+    args = [_pinned_ptr(a, nm, n) for a, nm in zip(h, names)] + [_pinned_ptr(out[0], "z0", n),
+                                                                 _pinned_ptr(out[1], "z1", n)]
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    _check(getattr(load(), "tf_" + name)(*args, n, st.cuda_stream), name)
+    st.synchronize()
+    return out
+
+
+def call_host(name, *host_arrays, out=None, device="cuda", mode="zero-copy"):
+    """End-to-end call on host arrays.  mode "zero-copy" (pinned float64 CPU
+    tensors): call_host_zero_copy.  mode "pipeline" (numpy or CPU tensors,
+    pinned for speed): copy in, run, copy (z0, z1) back, pipelined over chunks
     and streams (HostPipeline).  Returns CPU tensors (pinned when allocated here)."""
     import torch
     dev = torch.device(device)
+    if mode == "zero-copy":
+        return call_host_zero_copy(name, *host_arrays, out=out, device=dev)
     key = (dev.type, dev.index if dev.index is not None else torch.cuda.current_device())
     if key not in _pipes:
         _pipes[key] = HostPipeline(dev)

@@ -185,3 +185,19 @@ def test_full_size_sampled(tf, func):
     orc = oracle.evaluate(func, *sub)
     st = tfcheck.check(h0, h1, orc, "f64", 0.99999, f"{func} 2^26 sampled", func, sub)
     print(func, st)
+
+
+@pytest.mark.parametrize("func", UNARY + BINARY)
+@pytest.mark.parametrize("mode", ["zero-copy", "pipeline"])
+def test_host_api_equals_device_call(tf, func, mode):
+    """The host-array API (tf.call_host): the zero-copy mode, whose kernel reads
+    and writes pinned host memory directly, and the chunked copy pipeline give
+    the device call's results bit for bit, including a ragged last chunk."""
+    import torch
+    n = (1 << 22) + 4099
+    args = I.workload(func, n, start=77)
+    pin = [torch.from_numpy(a).pin_memory() for a in args]
+    z0, z1 = tf.call_host(func, *pin, mode=mode)
+    ref0, ref1 = run(tf, func, *args)
+    assert np.array_equal(z0.numpy().view(np.int64), ref0.view(np.int64))
+    assert np.array_equal(z1.numpy().view(np.int64), ref1.view(np.int64))
