@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-tier", action="store_true", help="skip the float/double precision-tier measurement")
     ap.add_argument("--no-sweep", action="store_true", help="skip the size sweep")
     ap.add_argument("--tier-log2n", type=int, default=28)
+    ap.add_argument("--sweep-max", type=int, default=26, choices=(26, 28, 30),
+                    help="largest size of the sweep (2^28 and 2^30 draw their own inputs: 4 / 16 GiB per array)")
     ap.add_argument("--funcs", default=",".join(FUNCS),
                     help="comma-separated subset (for profiling a single kernel)")
     return ap.parse_args()
@@ -300,18 +302,24 @@ def precision_tier(dev, log2n):
     return out
 
 
-def size_sweep(dev, dargs):
+def size_sweep(dev, dargs, max_lg=26):
     """texp and tlog (double) at n = 2^10 .. 2^26 (prefixes of the resident
-    2^26 inputs); up to 2^18 the timed unit is a CUDA graph of 64 launches, so
-    the host launch cost is out of the per-launch time."""
+    2^26 inputs), and up to 2^max_lg with inputs drawn for the purpose; up to
+    2^18 the timed unit is a CUDA graph of 64 launches, so the host launch cost
+    is out of the per-launch time."""
     import torch
-    from paper_1502_05216_gb300 import tf
+    from paper_1502_05216_gb300 import inputs as I, tf
     out = {}
     for func in ("texp", "tlog"):
         rows = []
-        for lg in (10, 14, 18, 22, 26):
+        for lg in (10, 14, 18, 22, 26, 28, 30):
+            if lg > max_lg:
+                break
             n = 1 << lg
-            a0, a1 = dargs[func][0][:n], dargs[func][1][:n]
+            if lg <= 26:
+                a0, a1 = dargs[func][0][:n], dargs[func][1][:n]
+            else:
+                a0, a1 = (torch.from_numpy(x).to(dev) for x in I.workload(func, n))
             o = (torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.float64, device=dev))
             if lg <= 18:
                 reps = 64
@@ -329,6 +337,10 @@ def size_sweep(dev, dargs):
             else:
                 ms = _time_launches(lambda: tf.FUNCS[func](a0, a1, out=o))
             rows.append({"n": n, "us": ms * 1e3, "gelem_s": n / (ms * 1e-3) / 1e9, "graph": lg <= 18})
+            del o
+            if lg > 26:
+                del a0, a1
+                torch.cuda.empty_cache()
         out[func] = rows
     return out
 
@@ -440,7 +452,7 @@ def ours(a, world, rank, local):
                "fp64_frac": FP64_PER_ELEM[f] * n / (kern_ms[f] * 1e-3) / peak,
                "hbm_gbs": BYTES_PER_ELEM[f] * n / (kern_ms[f] * 1e-3) / 1e9} for f in FUNCS}
     chain = None if a.no_chains else chains_bench(dev)
-    sweep = None if (a.no_sweep or a.log2n < 26 or "texp" not in dargs or "tlog" not in dargs) else size_sweep(dev, dargs)
+    sweep = None if (a.no_sweep or a.log2n < 26 or "texp" not in dargs or "tlog" not in dargs) else size_sweep(dev, dargs, a.sweep_max)
     tier = None if a.no_tier else precision_tier(dev, a.tier_log2n)
     cpu = None
     if world == 1 and not a.no_cpu_baseline:

@@ -201,3 +201,12 @@ def test_host_api_equals_device_call(tf, func, mode):
     ref0, ref1 = run(tf, func, *args)
     assert np.array_equal(z0.numpy().view(np.int64), ref0.view(np.int64))
     assert np.array_equal(z1.numpy().view(np.int64), ref1.view(np.int64))
+
+
+@pytest.mark.parametrize("func", ("texp", "tlog"))
+def test_hard_cases_2p24(tf, func):
+    """The 2^24-element hard-case set (thresholds, subnormal results, log near 1
+    and of subnormals, x1 = 0 and half-ulp x1, IEEE specials), every element
+    against the oracle."""
+    st = check(tf, func, I.hard_cases(func, 2**24, seed=29), f"{func} hard cases 2^24")
+    print(func, st)
