@@ -49,12 +49,6 @@ __device__ __forceinline__ tf2 sorted_two_sum(double a, double b) {
     return fast_two_sum(big, sml);
 }
 
-// TwoProduct with FMA: p + e == a * b exactly (barring underflow).
-__device__ __forceinline__ tf2 two_prod(double a, double b) {
-    double p = mul(a, b);
-    return {p, fma_rn(a, b, -p)};
-}
-
 // 2^k as a double for any int k: 0 below 2^-1074, +Inf above 2^1023, built from bits.
 __device__ __forceinline__ double pow2i(int k) {
     uint64_t normal = (uint64_t)(int64_t)(k + 1023) << 52;

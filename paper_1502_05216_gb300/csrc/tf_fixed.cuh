@@ -63,8 +63,6 @@ __device__ __forceinline__ u128 neg128(u128 a) { return sub128({0ull, 0ull}, a);
 
 __device__ __forceinline__ bool is_neg128(u128 a) { return (int64_t)a.hi < 0; }
 
-__device__ __forceinline__ u128 sel128(bool p, u128 a, u128 b) { return {p ? a.lo : b.lo, p ? a.hi : b.hi}; }
-
 // c + t or c - t by the sign flag.
 __device__ __forceinline__ u128 addsub128(u128 c, u128 t, bool minus) {
     return minus ? sub128(c, t) : add128(c, t);
