@@ -108,7 +108,7 @@ int tf_tadd(const double* x0, const double* x1, const double* y0, const double* 
 /* Twofold product z0 + z1 = (x0 + x1)(y0 + y1).
  * Paper: "Overview" (z0 = x0 (*) y0) and "Twofold exponent" > "Method summary"
  * (FMA-based exact product, 2 MUL + 1 FMA + 1 ADD per twofold-by-dotted step):
- * z1 = fma(x0, y0, -z0) + (x0 y1 + x1 y0); the x1 y1 term is dropped. */
+ * z1 = x0 y1 + x1 y0 + fma(x0, y0, -z0) (two FMAs); the x1 y1 term is dropped. */
 int tf_tmul(const double* x0, const double* x1, const double* y0, const double* y1,
             double* z0, double* z1, int64_t n, void* stream);
 

@@ -39,7 +39,11 @@ __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b);
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ uint32_t bits(float a) { return (uint32_t)__float_as_int(a); }
 __device__ __forceinline__ float from_bits(uint32_t b) { return __int_as_float((int)b); }
-__device__ __forceinline__ uint32_t absbits(float a) { return bits(a) & 0x7fffffffu; }
+__device__ __forceinline__ uint32_t absbits(float a) {  // kept on the integer ALU (see tf_eft.cuh)
+    uint32_t r;
+    asm("and.b32 %0, %1, 0x7fffffff;" : "=r"(r) : "r"(bits(a)));
+    return r;
+}
 
 constexpr uint32_t kExpMask = 0x7f800000u;
 constexpr uint32_t kSignMask = 0x80000000u;

@@ -21,7 +21,18 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 
 __device__ __forceinline__ uint64_t bits(double a) { return (uint64_t)__double_as_longlong(a); }
 __device__ __forceinline__ double from_bits(uint64_t b) { return __longlong_as_double((long long)b); }
-__device__ __forceinline__ uint64_t absbits(double a) { return bits(a) & 0x7fffffffffffffffull; }
+// Magnitude bits of a double.  The inline PTX keeps comparisons of these bits
+// on the integer ALU: the compiler may otherwise turn a compare of two
+// magnitude bit patterns into an FP64 compare, which occupies the FP64 pipe
+// (tadd, FP64-bound, ran at half speed that way).
+__device__ __forceinline__ uint64_t absbits(double a) {
+    uint64_t r;
+    asm("and.b64 %0, %1, 0x7fffffffffffffff;" : "=l"(r) : "l"(bits(a)));
+    return r;
+}
+// The plain form, which leaves the choice of compare to the compiler (used
+// where the integer ALU, not the FP64 pipe, is the busier unit).
+__device__ __forceinline__ uint64_t absbits_any(double a) { return bits(a) & 0x7fffffffffffffffull; }
 
 // Fast2Sum (Dekker): s + e == a + b exactly when a == 0 or exponent(a) >= exponent(b).
 // Three additions; the paper uses it for the "fast renormalization" (Twofold
