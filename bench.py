@@ -39,23 +39,29 @@ WORKLOAD = ("texp, texpm1, tlog, tlog1p (+ tadd, tmul) over double twofolds, n=2
 
 # FP64 pipe instructions (DADD + DMUL + DFMA, thread level) per element of each
 # kernel on its workload: ncu smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}
-# _pred_on.sum.per_cycle_elapsed x sm__cycles_elapsed.avg / n, from one
-# --set full capture at n = 2^25 (profiles/unary_v2_intcore_n2p25.md); tadd/tmul
-# are counted from the source (5 each).
-FP64_PER_ELEM = {"texp": 10.0, "texpm1": 12.0, "tlog": 26.0, "tlog1p": 33.0, "tadd": 5.0, "tmul": 5.0}
-FP64_COUNT_SOURCE = "ncu SASS counters (unary kernels), source count (tadd/tmul)"
+# _pred_on.sum.per_cycle_elapsed x smsp__cycles_elapsed.avg / n, from one
+# --set full capture per kernel at n = 2^25 (profiles/unary_v2_intcore_n2p25.md,
+# profiles/binary_v2_tadd_tmul_n2p25.md).  With the magnitude compares on the
+# integer ALU these are the only instructions of the kernels on the FP64 pipe
+# (the pipe's utilisation in the same capture matches them).
+FP64_PER_ELEM = {"texp": 9.0, "texpm1": 12.0, "tlog": 21.0, "tlog1p": 28.0, "tadd": 5.0, "tmul": 4.0}
+FP64_COUNT_SOURCE = "ncu SASS counters, one capture per kernel at n=2^25"
 # HBM bytes per element: SoA doubles in + out.
 BYTES_PER_ELEM = {"texp": 32, "texpm1": 32, "tlog": 32, "tlog1p": 32, "tadd": 48, "tmul": 48}
+HBM_PEAK_GBS = 6804.4   # MEASURED_PEAKS.json hbm_gbs (STREAM-style copy on the GB300s)
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# same capture at n = 2^25, scaled by 2 to the benchmark's n = 2^26 (the traffic
+# same captures at n = 2^25, scaled by 2 to the benchmark's n = 2^26 (the traffic
 # of an elementwise kernel is proportional to n).  The writes still held in L2 when
 # a launch ends are not in its count.
-TRAFFIC_PER_LAUNCH = {"texp": 2.0472e9, "texpm1": 2.0459e9, "tlog": 2.0491e9, "tlog1p": 2.0492e9}
+TRAFFIC_PER_LAUNCH = {"texp": 2.0489e9, "texpm1": 2.0442e9, "tlog": 2.0438e9, "tlog1p": 2.0476e9,
+                      "tadd": 3.1480e9, "tmul": 3.1481e9}
 TRAFFIC_N = 1 << 26
-# Pipe utilisation of the same capture (sm__inst_executed_pipe_{fp64,alu}, % of
-# peak while active): the kernels are co-limited by the FP64 and integer pipes.
-PIPES = {"texp": {"fp64_pct": 55.6, "alu_pct": 78.3}, "texpm1": {"fp64_pct": 60.4, "alu_pct": 80.5},
-         "tlog": {"fp64_pct": 65.4, "alu_pct": 77.5}, "tlog1p": {"fp64_pct": 73.6, "alu_pct": 73.0}}
+# Pipe utilisation of the same captures (sm__inst_executed_pipe_{fp64,alu}, % of
+# peak while active): the unary kernels are co-limited by the FP64 and integer
+# pipes, tadd and tmul by the FP64 pipe and HBM.
+PIPES = {"texp": {"fp64_pct": 50.0, "alu_pct": 78.6}, "texpm1": {"fp64_pct": 60.3, "alu_pct": 80.5},
+         "tlog": {"fp64_pct": 58.8, "alu_pct": 79.9}, "tlog1p": {"fp64_pct": 67.8, "alu_pct": 75.7},
+         "tadd": {"fp64_pct": 83.2, "alu_pct": 17.4}, "tmul": {"fp64_pct": 93.4, "alu_pct": 18.6}}
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -293,7 +299,7 @@ def precision_tier(dev, log2n):
             o = (torch.empty_like(d0), torch.empty_like(d0))
             ms = _time_launches(lambda: fn(d0, d1, out=o))
             res[dt] = {"ms": ms, "gelem_s": n / (ms * 1e-3) / 1e9, "hbm_gbs": bpe * n / (ms * 1e-3) / 1e9,
-                       "hbm_frac": bpe * n / (ms * 1e-3) / 1e9 / 6804.4}
+                       "hbm_frac": bpe * n / (ms * 1e-3) / 1e9 / HBM_PEAK_GBS}
             del d0, d1, o
         res["f32_over_f64"] = res["f64"]["ms"] / res["f32"]["ms"]
         out[func] = res
@@ -446,11 +452,16 @@ def ours(a, world, rank, local):
             "traffic": TRAFFIC_PER_LAUNCH.get(dom) if n == TRAFFIC_N else None,
             "traffic_source": "ncu dram bytes of one launch at n=2^25, x2" if n == TRAFFIC_N else None,
             "ncu_pipes_pct": PIPES.get(dom),
-            "hbm_view": {"achieved_gbs": BYTES_PER_ELEM[dom] * n / d / 1e9, "peak_gbs": 6804.4,
+            "hbm_view": {"achieved_gbs": BYTES_PER_ELEM[dom] * n / d / 1e9, "peak_gbs": HBM_PEAK_GBS,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}
-    per = {f: {"ms": kern_ms[f], "gelem_s": n / (kern_ms[f] * 1e-3) / 1e9,
-               "fp64_frac": FP64_PER_ELEM[f] * n / (kern_ms[f] * 1e-3) / peak,
-               "hbm_gbs": BYTES_PER_ELEM[f] * n / (kern_ms[f] * 1e-3) / 1e9} for f in FUNCS}
+    per = {}
+    for f in FUNCS:
+        t = kern_ms[f] * 1e-3
+        fp64_frac = FP64_PER_ELEM[f] * n / t / peak
+        hbm_frac = BYTES_PER_ELEM[f] * n / t / 1e9 / HBM_PEAK_GBS
+        per[f] = {"ms": kern_ms[f], "gelem_s": n / t / 1e9, "fp64_frac": fp64_frac,
+                  "hbm_gbs": BYTES_PER_ELEM[f] * n / t / 1e9, "hbm_frac": hbm_frac,
+                  "binding": "fp64" if fp64_frac >= hbm_frac else "hbm", "binding_frac": max(fp64_frac, hbm_frac)}
     chain = None if a.no_chains else chains_bench(dev)
     sweep = None if (a.no_sweep or a.log2n < 26 or "texp" not in dargs or "tlog" not in dargs) else size_sweep(dev, dargs, a.sweep_max)
     tier = None if a.no_tier else precision_tier(dev, a.tier_log2n)

@@ -27,15 +27,17 @@ nearest, each with its unit):
       m = 0 .. 4 in units 2^-127 as (lo64, hi64), m = 5 .. 9 in units 2^-72.
   TF_C12FIX    ln2/256 - C0 (> 0), units 2^-148: the tail of the reduction constant.
   TF_LN2FIX    ln2, units 2^-128 (the n ln2 term of the logarithm).
-  TF_LOGTAB[i] for i = 724 .. 1448 (z = i/1024 covers [sqrt(1/2), sqrt(2))):
-      {log(c_i) in units 2^-64 (two's complement), C_i} with c_i = C_i 2^-24,
-      C_i = round(2^34 / i): the reciprocal table of the 1x logarithm seed,
-      log z = log1p(z c_i - 1) - log c_i with |z c_i - 1| < 2^-10.4.
+  TF_LOGT[i] for i = 724 .. 1448 (z = i/1024 covers [sqrt(1/2), sqrt(2))):
+      {-log(c_i) in units 2^-128 as a two's complement (lo64, hi64), C_i, the
+      bits of c_i as a double} with c_i = C_i 2^-24, C_i = round(2^34 / i): the
+      reciprocal table of the logarithm, log z = -log c_i + log1p(t) with
+      t = z c_i - 1 exact and |t| < 2^-10.4.
   TF_LG_m      (-1)^m / (m+1), m = 0 .. 5, units 2^-62 (two's complement): the
       coefficients of log1p(t)/t.
 """
 import decimal
 import math
+import struct
 import sys
 
 D = decimal.Decimal
@@ -144,14 +146,22 @@ def main(out=sys.stdout):
     for m in range(0, 6):
         x = fixed(CTX.divide(D((-1) ** m), D(m + 1)), 62)
         w(f"#define TF_LG_{m} ((long long)0x{x & (2**64 - 1):016x}ull)\n")
-    w("\n#define TF_LOGTAB_LO 724\n#define TF_LOGTAB_HI 1448\n")
-    w("/* {log(c_i) units 2^-64 (two's complement), C_i} for i = 724 .. 1448, c_i = C_i 2^-24 */\n")
-    w("TF_TABLE_QUALIFIER long long TF_LOGTAB[725][2] = {\n")
+    w("\n#define TF_LOGT_LO 724\n#define TF_LOGT_HI 1448\n")
+    w("/* {-log(c_i) units 2^-128 as (lo64, hi64), C_i, bits of c_i} for i = 724 .. 1448,\n"
+      "   c_i = C_i 2^-24 */\n")
+    w("TF_TABLE_QUALIFIER unsigned long long TF_LOGT[725][4] = {\n")
     for i in range(724, 1449):
         C = int(CTX.divide(D(2**34), D(i)).to_integral_value(rounding=decimal.ROUND_HALF_EVEN))
-        lc = fixed(CTX.ln(CTX.divide(D(C), D(2**24))), 64)
-        assert abs(lc) < 2**63 and C < 2**25
-        w(f"  {{(long long)0x{lc & (2**64 - 1):016x}ull, {C}}},\n")
+        c = CTX.divide(D(C), D(2**24))
+        L = fixed(CTX.minus(CTX.ln(c)), 128)
+        assert abs(L) < 2**126.5 and C < 2**25
+        z_lo, z_hi = D(i) / 1024 - D(1) / 2048, D(i) / 1024 + D(1) / 2048
+        for zz in (max(z_lo, D("0.70710678118654752440")), min(z_hi, D("1.41421356237309504880"))):
+            assert abs(CTX.subtract(CTX.multiply(zz, c), 1)) < D(2) ** D("-10.4"), (i, zz)
+        cd = float(c)
+        assert D(cd) == c
+        Lu = L & (2**128 - 1)
+        w(f"  {{0x{Lu & (2**64 - 1):016x}ull, 0x{Lu >> 64:016x}ull, {C}ull, 0x{struct.unpack('<Q', struct.pack('<d', cd))[0]:016x}ull}},\n")
     w("};\n\n")
     w("/* 2^(j/256) in units of 2^-127 as {lo64, hi64}; index j + 128 */\n")
     w("TF_TABLE_QUALIFIER unsigned long long TF_TFIX_TABLE[257][2] = {\n")

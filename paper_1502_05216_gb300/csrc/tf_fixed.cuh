@@ -91,6 +91,29 @@ __device__ __forceinline__ u128 shl128_var(u128 a, int s) {
     return {a.lo << s, (a.hi << s) | carry};
 }
 
+// Logical shift right by any run-time s >= 0 (0 from s >= 128).
+__device__ __forceinline__ u128 shr128_any(u128 a, int s) {
+    int s1 = min(s, 63);
+    int s2 = min(max(s - 64, 0), 63);
+    uint64_t lo = (s < 64) ? ((a.lo >> s1) | ((a.hi << 1) << (63 - s1))) : ((s < 128) ? (a.hi >> s2) : 0ull);
+    uint64_t hi = (s < 64) ? (a.hi >> s1) : 0ull;
+    return {lo, hi};
+}
+
+// Arithmetic (sign-extending) shift right of a two's complement value by a
+// compile-time 0 < s < 64.
+template <int s>
+__device__ __forceinline__ u128 sar128(u128 a) {
+    return {(a.lo >> s) | (a.hi << (64 - s)), (uint64_t)((int64_t)a.hi >> s)};
+}
+
+// a * b for a < 2^64 and a 32-bit b: two IMAD.WIDE.U32.
+__device__ __forceinline__ u128 mul_u64_u32(uint64_t a, uint32_t b) {
+    uint64_t p0 = mad_wide((uint32_t)a, b, 0ull);
+    uint64_t p1 = mad_wide((uint32_t)(a >> 32), b, p0 >> 32);
+    return {(p1 << 32) | (uint32_t)p0, p1 >> 32};
+}
+
 // A 53-bit (or shorter) integer m shifted by s bits, left for s >= 0 and right
 // (truncating) for s < 0; s <= 74 keeps the result below 2^127.
 __device__ __forceinline__ u128 place53(uint64_t m, int s) {

@@ -5,29 +5,27 @@
 
 namespace {
 
-__global__ void dfma_chains(double* out, int iters) {
-    // Eight independent chains a <- a * m + c with m slightly below 1 and a small
-    // c: the values stay bounded, so no special operands slow the pipe.
-    const double m = 0.99999999999;
-    const double c = 1e-12 * (threadIdx.x + 1);
-    double a0 = 1.0, a1 = 1.1, a2 = 1.2, a3 = 1.3, a4 = 1.4, a5 = 1.5, a6 = 1.6, a7 = 1.7;
+// Eight independent chains a <- a * m + c per thread.  m slightly below 1 and a
+// small c keep the values bounded, so no special operands slow the pipe.  m and
+// c arrive as kernel arguments: with a literal multiplier and a per-thread
+// addend the same loop ran at only about 1.7 DFMA per clock per SM on GB300,
+// against 2 with both operands uniform.
+__global__ void dfma_chains(double* out, int iters, double m, double c) {
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 1.0 + 0.1 * k + 1e-9 * threadIdx.x;
     for (int i = 0; i < iters; ++i) {
-        a0 = __fma_rn(a0, m, c);
-        a1 = __fma_rn(a1, m, c);
-        a2 = __fma_rn(a2, m, c);
-        a3 = __fma_rn(a3, m, c);
-        a4 = __fma_rn(a4, m, c);
-        a5 = __fma_rn(a5, m, c);
-        a6 = __fma_rn(a6, m, c);
-        a7 = __fma_rn(a7, m, c);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = __fma_rn(a[k], m, c);
     }
-    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] =
+        ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
 }  // namespace
 
 extern "C" int tfp_dfma(double* out, int blocks, int threads, int iters, void* stream) {
     if (!out || blocks <= 0 || threads <= 0 || threads > 1024 || iters <= 0) return 6;
-    dfma_chains<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(out, iters);
+    dfma_chains<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(out, iters, 0.99999999999, 1e-12);
     return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }
