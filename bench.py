@@ -37,31 +37,36 @@ WORKLOAD = ("texp, texpm1, tlog, tlog1p (+ tadd, tmul) over double twofolds, n=2
             "args random sign |x0| log-uniform in [2^-40, 708]; log x0 log-uniform in [2^-1020, 2^1020]; "
             "log1p half |x0| log-uniform in [2^-40, 2^-10), half -1+2^-30 .. 2^100; x1 = x0*u*2^-53")
 
-# FP64 pipe instructions (DADD + DMUL + DFMA, thread level) per element of each
-# kernel on its workload: ncu smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}
-# _pred_on.sum.per_cycle_elapsed x smsp__cycles_elapsed.avg / n, from one
+# Per-element instruction counts of each kernel on its workload, from one ncu
 # --set full capture per kernel at n = 2^25 (profiles/unary_v2_intcore_n2p25.md,
-# profiles/binary_v2_tadd_tmul_n2p25.md).  With the magnitude compares on the
-# integer ALU these are the only instructions of the kernels on the FP64 pipe
-# (the pipe's utilisation in the same capture matches them).
-FP64_PER_ELEM = {"texp": 9.0, "texpm1": 12.0, "tlog": 21.0, "tlog1p": 28.0, "tadd": 5.0, "tmul": 4.0}
-FP64_COUNT_SOURCE = "ncu SASS counters, one capture per kernel at n=2^25"
+# profiles/binary_v2_tadd_tmul_n2p25.md):
+# * FP64-pipe thread instructions: smsp__sass_thread_inst_executed_op_{dadd,dmul,
+#   dfma}_pred_on (the dadd class includes FP64 compares) x cycles / n; it equals
+#   sm__inst_executed_pipe_fp64 utilisation x 2 per SM per cycle x cycles / n;
+# * integer-ALU-pipe thread instructions: sm__inst_executed_pipe_alu utilisation
+#   x 64 per SM per cycle x active cycles / n (16 lanes per SM sub-partition: the
+#   same derivation with the issue rate reproduces smsp__inst_executed exactly).
+FP64_PER_ELEM = {"texp": 9.0, "texpm1": 13.0, "tlog": 17.0, "tlog1p": 23.0, "tadd": 5.0, "tmul": 4.0}
+ALU_PER_ELEM = {"texp": 346.0, "texpm1": 439.0, "tlog": 526.0, "tlog1p": 630.0, "tadd": 34.0, "tmul": 26.0}
+COUNT_SOURCE = "ncu pipe counters, one --set full capture per kernel at n=2^25"
+ALU_LANES_PER_SM_CLK = 64
 # HBM bytes per element: SoA doubles in + out.
 BYTES_PER_ELEM = {"texp": 32, "texpm1": 32, "tlog": 32, "tlog1p": 32, "tadd": 48, "tmul": 48}
 HBM_PEAK_GBS = 6804.4   # MEASURED_PEAKS.json hbm_gbs (STREAM-style copy on the GB300s)
+SM_MAX_MHZ = 2070.0     # MEASURED_PEAKS.json sm_max_mhz (used when no clock sample exists)
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # same captures at n = 2^25, scaled by 2 to the benchmark's n = 2^26 (the traffic
 # of an elementwise kernel is proportional to n).  The writes still held in L2 when
 # a launch ends are not in its count.
-TRAFFIC_PER_LAUNCH = {"texp": 2.0489e9, "texpm1": 2.0442e9, "tlog": 2.0438e9, "tlog1p": 2.0476e9,
+TRAFFIC_PER_LAUNCH = {"texp": 2.0478e9, "texpm1": 2.0448e9, "tlog": 2.0474e9, "tlog1p": 2.0515e9,
                       "tadd": 3.1480e9, "tmul": 3.1481e9}
 TRAFFIC_N = 1 << 26
-# Pipe utilisation of the same captures (sm__inst_executed_pipe_{fp64,alu}, % of
-# peak while active): the unary kernels are co-limited by the FP64 and integer
-# pipes, tadd and tmul by the FP64 pipe and HBM.
-PIPES = {"texp": {"fp64_pct": 50.0, "alu_pct": 78.6}, "texpm1": {"fp64_pct": 60.3, "alu_pct": 80.5},
-         "tlog": {"fp64_pct": 58.8, "alu_pct": 79.9}, "tlog1p": {"fp64_pct": 67.8, "alu_pct": 75.7},
-         "tadd": {"fp64_pct": 83.2, "alu_pct": 17.4}, "tmul": {"fp64_pct": 93.4, "alu_pct": 18.6}}
+# Pipe utilisation of the same captures (% of peak while active): the unary
+# kernels are co-limited by the integer ALU and FP64 pipes (exp: ALU first;
+# log1p: FP64 first), tadd by the FP64 pipe, tmul by the FP64 pipe and HBM.
+PIPES = {"texp": {"alu_pct": 70.1, "fp64_pct": 58.4}, "texpm1": {"alu_pct": 72.6, "fp64_pct": 68.8},
+         "tlog": {"alu_pct": 72.8, "fp64_pct": 75.3}, "tlog1p": {"alu_pct": 69.5, "fp64_pct": 81.2},
+         "tadd": {"alu_pct": 17.4, "fp64_pct": 83.2}, "tmul": {"alu_pct": 18.6, "fp64_pct": 93.4}}
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -444,24 +449,37 @@ def ours(a, world, rank, local):
         return
     dom = max(FUNCS, key=lambda f: kern_ms[f])
     d = kern_ms[dom] * 1e-3
-    achieved = FP64_PER_ELEM[dom] * n / d / 1e9
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak / 1e9,
-            "unit": "FP64 Ginst/s", "frac": achieved / (peak / 1e9),
-            "peak_source": f"measured: DFMA calibration kernel on this GPU ({sms} SMs)",
-            "fp64_inst_per_elem": FP64_PER_ELEM[dom], "fp64_count_source": FP64_COUNT_SOURCE,
+    mhz = ck.get("sm_mhz") or SM_MAX_MHZ
+    alu_peak = ALU_LANES_PER_SM_CLK * sms * mhz * 1e6
+    views = {
+        "integer": {"achieved": ALU_PER_ELEM[dom] * n / d / 1e9, "peak": alu_peak / 1e9,
+                    "unit": "integer-ALU-pipe Ginst/s", "inst_per_elem": ALU_PER_ELEM[dom],
+                    "peak_source": f"derived: {ALU_LANES_PER_SM_CLK} integer-ALU lanes per SM per clock x {sms} SMs x "
+                                   f"{mhz:.0f} MHz ({'median SM clock sampled in the timed region' if ck.get('sm_mhz') else 'SM max clock'})"},
+        "fp64": {"achieved": FP64_PER_ELEM[dom] * n / d / 1e9, "peak": peak / 1e9, "unit": "FP64 Ginst/s",
+                 "inst_per_elem": FP64_PER_ELEM[dom],
+                 "peak_source": f"measured: DFMA calibration kernel on this GPU ({sms} SMs)"},
+    }
+    for v in views.values():
+        v["frac"] = v["achieved"] / v["peak"]
+    pipe = max(views, key=lambda k: views[k]["frac"])
+    other = "fp64" if pipe == "integer" else "integer"
+    roof = {"bound": "alu", "pipe": pipe, "kernel": dom, **views[pipe], "count_source": COUNT_SOURCE,
             "traffic": TRAFFIC_PER_LAUNCH.get(dom) if n == TRAFFIC_N else None,
             "traffic_source": "ncu dram bytes of one launch at n=2^25, x2" if n == TRAFFIC_N else None,
-            "ncu_pipes_pct": PIPES.get(dom),
+            "ncu_pipes_pct": PIPES.get(dom), f"{other}_view": views[other],
             "hbm_view": {"achieved_gbs": BYTES_PER_ELEM[dom] * n / d / 1e9, "peak_gbs": HBM_PEAK_GBS,
+                         "frac": BYTES_PER_ELEM[dom] * n / d / 1e9 / HBM_PEAK_GBS,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}
     per = {}
     for f in FUNCS:
         t = kern_ms[f] * 1e-3
-        fp64_frac = FP64_PER_ELEM[f] * n / t / peak
-        hbm_frac = BYTES_PER_ELEM[f] * n / t / 1e9 / HBM_PEAK_GBS
-        per[f] = {"ms": kern_ms[f], "gelem_s": n / t / 1e9, "fp64_frac": fp64_frac,
-                  "hbm_gbs": BYTES_PER_ELEM[f] * n / t / 1e9, "hbm_frac": hbm_frac,
-                  "binding": "fp64" if fp64_frac >= hbm_frac else "hbm", "binding_frac": max(fp64_frac, hbm_frac)}
+        fr = {"alu": ALU_PER_ELEM[f] * n / t / alu_peak, "fp64": FP64_PER_ELEM[f] * n / t / peak,
+              "hbm": BYTES_PER_ELEM[f] * n / t / 1e9 / HBM_PEAK_GBS}
+        b = max(fr, key=fr.get)
+        per[f] = {"ms": kern_ms[f], "gelem_s": n / t / 1e9, "hbm_gbs": BYTES_PER_ELEM[f] * n / t / 1e9,
+                  "alu_frac": fr["alu"], "fp64_frac": fr["fp64"], "hbm_frac": fr["hbm"],
+                  "binding": b, "binding_frac": fr[b]}
     chain = None if a.no_chains else chains_bench(dev)
     sweep = None if (a.no_sweep or a.log2n < 26 or "texp" not in dargs or "tlog" not in dargs) else size_sweep(dev, dargs, a.sweep_max)
     tier = None if a.no_tier else precision_tier(dev, a.tier_log2n)

@@ -19,18 +19,22 @@ namespace {
 constexpr int kThreads = 256;
 
 struct OpExp {
+    static constexpr int min_blocks = 4;  // 64 registers: 32 warps per SM
     static constexpr double dummy = 0.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp1(a, b, z0, z1); }
 };
 struct OpExpm1 {
+    static constexpr int min_blocks = 4;  // 64 registers: 32 warps per SM
     static constexpr double dummy = 0.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texpm11(a, b, z0, z1); }
 };
 struct OpLog {
+    static constexpr int min_blocks = 4;  // 64 registers: 32 warps per SM
     static constexpr double dummy = 1.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1(a, b, z0, z1); }
 };
 struct OpLog1p {
+    static constexpr int min_blocks = 4;  // 64 registers: 32 warps per SM
     static constexpr double dummy = 0.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1p1(a, b, z0, z1); }
 };
@@ -69,7 +73,7 @@ __device__ __forceinline__ void st2(double* p, double a, double b) {
 
 // Unary, 2 elements per thread, 128-bit I/O.  Thread t covers elements 2t, 2t+1.
 template <class Op>
-__global__ void __launch_bounds__(kThreads) unary_v2(const double* __restrict__ x0, const double* __restrict__ x1,
+__global__ void __launch_bounds__(kThreads, Op::min_blocks) unary_v2(const double* __restrict__ x0, const double* __restrict__ x1,
                                                      double* z0, double* z1, int64_t n) {
     int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     int64_t i = 2 * t;
