@@ -46,8 +46,8 @@ WORKLOAD = ("texp, texpm1, tlog, tlog1p (+ tadd, tmul) over double twofolds, n=2
 # * integer-ALU-pipe thread instructions: sm__inst_executed_pipe_alu utilisation
 #   x 64 per SM per cycle x active cycles / n (16 lanes per SM sub-partition: the
 #   same derivation with the issue rate reproduces smsp__inst_executed exactly).
-FP64_PER_ELEM = {"texp": 9.0, "texpm1": 13.0, "tlog": 17.0, "tlog1p": 23.0, "tadd": 5.0, "tmul": 4.0}
-ALU_PER_ELEM = {"texp": 346.0, "texpm1": 439.0, "tlog": 526.0, "tlog1p": 630.0, "tadd": 34.0, "tmul": 26.0}
+FP64_PER_ELEM = {"texp": 9.0, "texpm1": 13.0, "tlog": 12.0, "tlog1p": 18.0, "tadd": 5.0, "tmul": 4.0}
+ALU_PER_ELEM = {"texp": 345.0, "texpm1": 439.0, "tlog": 525.0, "tlog1p": 605.0, "tadd": 34.0, "tmul": 26.0}
 COUNT_SOURCE = "ncu pipe counters, one --set full capture per kernel at n=2^25"
 ALU_LANES_PER_SM_CLK = 64
 # HBM bytes per element: SoA doubles in + out.
@@ -58,14 +58,14 @@ SM_MAX_MHZ = 2070.0     # MEASURED_PEAKS.json sm_max_mhz (used when no clock sam
 # same captures at n = 2^25, scaled by 2 to the benchmark's n = 2^26 (the traffic
 # of an elementwise kernel is proportional to n).  The writes still held in L2 when
 # a launch ends are not in its count.
-TRAFFIC_PER_LAUNCH = {"texp": 2.0478e9, "texpm1": 2.0448e9, "tlog": 2.0474e9, "tlog1p": 2.0515e9,
+TRAFFIC_PER_LAUNCH = {"texp": 2.0479e9, "texpm1": 2.0438e9, "tlog": 2.0444e9, "tlog1p": 2.0537e9,
                       "tadd": 3.1480e9, "tmul": 3.1481e9}
 TRAFFIC_N = 1 << 26
 # Pipe utilisation of the same captures (% of peak while active): the unary
-# kernels are co-limited by the integer ALU and FP64 pipes (exp: ALU first;
-# log1p: FP64 first), tadd by the FP64 pipe, tmul by the FP64 pipe and HBM.
+# kernels are bound by the integer ALU pipe with the FP64 pipe second, tadd by
+# the FP64 pipe, tmul by the FP64 pipe and HBM together.
 PIPES = {"texp": {"alu_pct": 70.1, "fp64_pct": 58.4}, "texpm1": {"alu_pct": 72.6, "fp64_pct": 68.8},
-         "tlog": {"alu_pct": 72.8, "fp64_pct": 75.3}, "tlog1p": {"alu_pct": 69.5, "fp64_pct": 81.2},
+         "tlog": {"alu_pct": 74.6, "fp64_pct": 54.5}, "tlog1p": {"alu_pct": 74.4, "fp64_pct": 70.8},
          "tadd": {"alu_pct": 17.4, "fp64_pct": 83.2}, "tmul": {"alu_pct": 18.6, "fp64_pct": 93.4}}
 
 def parse():
@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-chains", action="store_true", help="skip the batched-chains measurement")
     ap.add_argument("--no-tier", action="store_true", help="skip the float/double precision-tier measurement")
+    ap.add_argument("--no-coupled", action="store_true",
+                    help="skip the coupled-result / coupled-argument variants (pexp ... tlog1pp)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the size sweep")
     ap.add_argument("--tier-log2n", type=int, default=28)
     ap.add_argument("--sweep-max", type=int, default=26, choices=(26, 28, 30),
@@ -285,6 +287,34 @@ def _time_launches(fn, reps=5, warm=3):
     return statistics.median(ts)
 
 
+def coupled_variants(dev, dargs, n, reps=5):
+    """Kernel time of the coupled-result (pexp, pexpm1, plog, plog1p) and
+    coupled-argument (texpp, texpm1p, tlogp, tlog1pp) entry points on the same
+    inputs as their twofold functions, CUDA events, mean of ``reps`` launches
+    after one warm-up."""
+    import torch
+    from paper_1502_05216_gb300 import tf
+    st = torch.cuda.current_stream(dev)
+    z0 = torch.empty(n, dtype=torch.float64, device=dev)
+    z1 = torch.empty_like(z0)
+    out = {}
+    for name, fn in tf.FUNCS_C.items():
+        base = tf.BASE_OF[name]
+        res = {}
+        for key, f in ((name, fn), (base, tf.FUNCS[base])):
+            f(*dargs[base], out=(z0, z1), stream=st)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                f(*dargs[base], out=(z0, z1), stream=st)
+            e1.record(st)
+            e1.synchronize()
+            res[key] = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": res[name], "gelem_s": n / (res[name] * 1e-3) / 1e9, "twofold": base,
+                     "twofold_ms": res[base], "time_ratio": res[name] / res[base]}
+    return out
+
+
 def precision_tier(dev, log2n):
     """texp and tlog over float twofolds (float-float on the FP32 pipes) and
     over double twofolds (the FP64 + integer path) on the same x0 values, n =
@@ -483,6 +513,8 @@ def ours(a, world, rank, local):
     chain = None if a.no_chains else chains_bench(dev)
     sweep = None if (a.no_sweep or a.log2n < 26 or "texp" not in dargs or "tlog" not in dargs) else size_sweep(dev, dargs, a.sweep_max)
     tier = None if a.no_tier else precision_tier(dev, a.tier_log2n)
+    coupled = (None if a.no_coupled or not {"texp", "texpm1", "tlog", "tlog1p"} <= set(dargs)
+               else coupled_variants(dev, dargs, n))
     cpu = None
     if world == 1 and not a.no_cpu_baseline:
         rate, cores, sample, _, _ = oracle_rate(12.0)
@@ -495,7 +527,7 @@ def ours(a, world, rank, local):
                    "l2": "no flush: every input array (512 MiB) is larger than L2", "parallelism": f"dp{world}"},
         "roofline": roof, "per_func": per, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": len(FUNCS) * a.steps, "clocks": ck, "chains": chain, "precision_tier": tier,
-        "size_sweep": sweep,
+        "size_sweep": sweep, "coupled_variants": coupled,
     }), flush=True)
 
 

@@ -72,7 +72,9 @@ int tf_texpm1(const double* x0, const double* x1, double* z0, double* z1, int64_
 
 /* Twofold logarithm z0 + z1 = log(y0 + y1).
  * Paper: "Twofold logarithm" > "Newton inversion" and "Algorithm summary"
- * (tlog, plog, tlog0): one Newton step on e^x seeded by a 1x-precise log1p.
+ * (tlog, plog, tlog0): y0 = 2^n z, log z = -log c_i + log1p(z c_i - 1) with a
+ * reciprocal table c_i, and one Newton step on e^x seeded by a 1x-precise
+ * log1p of the reduced argument.
  * z0 = RN(log y0); y0 < 0 or NaN gives NaN, y0 = +-0 gives -Inf (z1 = 0).
  * y1 may be any double: a twofold that is not renormalised takes a slower
  * path in its warp. */
@@ -83,6 +85,31 @@ int tf_tlog(const double* y0, const double* y1, double* z0, double* z1, int64_t 
  * (tlog1p, plog1p, tlog1p0): Newton step on e^x - 1.  z0 = RN(log1p y0);
  * y0 < -1 gives NaN, y0 = -1 gives -Inf (z1 = 0). */
 int tf_tlog1p(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
+
+/* Coupled results.  Paper: "Twofold exponent" > "Algorithm summary" (pexp,
+ * pexpm1: "coupled exponent of coupled argument") and "Twofold logarithm" >
+ * "Algorithm summary" (plog, plog1p).  z0 + z1 is the same 2x-precise value as
+ * the twofold function's, renormalised: z0 = RN(z0 + z1) (so z0 is the
+ * correctly rounded f(x0 + x1) unless that lies within about 2^-106 relative
+ * of a rounding midpoint) and z1 the exact remainder.  x1 = NULL gives pexp0,
+ * pexpm10, plog0, plog1p0.  Special results (z0 or z1 not finite) and z1 = 0
+ * are returned as the twofold function returns them.  Same contract as tf_texp. */
+int tf_pexp(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream);
+int tf_pexpm1(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream);
+int tf_plog(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
+int tf_plog1p(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
+
+/* Twofold results of coupled arguments.  Paper: texpp, texpm1p ("twofold
+ * exponent of coupled argument"), tlogp, tlog1pp ("coupled argument,
+ * |y1| << |y0|").  As tf_texp, tf_texpm1, tf_tlog, tf_tlog1p, except that the
+ * argument is taken as coupled (|x1| at most about 2^-30 |x0|; 2^-20 for
+ * tlog1pp relative to 1 + y0): the renormalising path for a loose x1 is not
+ * taken, so for a loose argument z1 is only first-order accurate.  Non-finite
+ * x1 keep the twofold functions' rules. */
+int tf_texpp(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream);
+int tf_texpm1p(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream);
+int tf_tlogp(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
+int tf_tlog1pp(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
 
 /* Float twofolds: the same four functions over pairs of floats, with the
  * paper's "f"-suffixed float variants in mind ("Twofold exponent" and

@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import ctypes
 import decimal
+from fractions import Fraction
 import os
 import subprocess
 import threading
@@ -137,6 +138,27 @@ def evaluate(func: str, x0, x1=None, y0=None, y1=None, lib=None, dtype: str = "f
                 Z0[i] = z
     fl &= ~np.uint32(FL_AMBIG)
     return Result(Z0, Gh, Gl, A, fl)
+
+
+def coupled(res: Result) -> Result:
+    """The coupled form of a twofold answer (paper, "Algorithm summary" of the
+    exponent and of the logarithm: pexp, pexpm1, plog, plog1p return the
+    "coupled" value of f): with F = Z0 + Gh + Gl, the main part becomes RN(F)
+    and Gh + Gl the remainder F - RN(F).  Exact rational arithmetic, element by
+    element.  Answers fixed by the special-value rules (FL_EXACT), non-finite
+    parts and G = 0 (already coupled) are returned unchanged."""
+    Z0, Gh, Gl = res.Z0.copy(), res.Gh.copy(), res.Gl.copy()
+    for i in range(Z0.size):
+        if (res.flags[i] & FL_EXACT) or not (np.isfinite(Z0[i]) and np.isfinite(Gh[i]) and np.isfinite(Gl[i])):
+            continue
+        if Gh[i] == 0.0 and Gl[i] == 0.0:
+            continue
+        F = Fraction(float(Z0[i])) + Fraction(float(Gh[i])) + Fraction(float(Gl[i]))
+        z = float(F)                     # correctly rounded (integer true division)
+        r = F - Fraction(z)
+        h = float(r)
+        Z0[i], Gh[i], Gl[i] = z, h, float(r - Fraction(h))
+    return Result(Z0, Gh, Gl, res.A.copy(), res.flags.copy())
 
 
 def chain(batch: dict, lib=None):

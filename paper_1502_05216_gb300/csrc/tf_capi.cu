@@ -38,6 +38,60 @@ struct OpLog1p {
     static constexpr double dummy = 0.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1p1(a, b, z0, z1); }
 };
+// Coupled results (pexp, pexpm1, plog, plog1p) and twofold results of coupled
+// arguments (texpp, texpm1p, tlogp, tlog1pp).
+struct OpPExp {
+    static constexpr double dummy = 0.0;
+    static constexpr int min_blocks = 4;
+    __device__ static void eval(double a, double b, double& z0, double& z1) {
+        tf::texp_impl<true>(a, b, z0, z1);
+        tf::couple(z0, z1);
+    }
+};
+struct OpPExpm1 {
+    static constexpr double dummy = 0.0;
+    static constexpr int min_blocks = 4;
+    __device__ static void eval(double a, double b, double& z0, double& z1) {
+        tf::texpm1_impl<true>(a, b, z0, z1);
+        tf::couple(z0, z1);
+    }
+};
+struct OpPLog {
+    static constexpr double dummy = 1.0;
+    static constexpr int min_blocks = 4;
+    __device__ static void eval(double a, double b, double& z0, double& z1) {
+        tf::tlog_impl<true>(a, b, z0, z1);
+        tf::couple(z0, z1);
+    }
+};
+struct OpPLog1p {
+    static constexpr double dummy = 0.0;
+    static constexpr int min_blocks = 4;
+    __device__ static void eval(double a, double b, double& z0, double& z1) {
+        tf::tlog1p1(a, b, z0, z1);
+        tf::couple(z0, z1);
+    }
+};
+struct OpExpP {
+    static constexpr double dummy = 0.0;
+    static constexpr int min_blocks = 4;
+    __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp_impl<true, false>(a, b, z0, z1); }
+};
+struct OpExpm1P {
+    static constexpr double dummy = 0.0;
+    static constexpr int min_blocks = 4;
+    __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texpm1_impl<true, false>(a, b, z0, z1); }
+};
+struct OpLogP {
+    static constexpr double dummy = 1.0;
+    static constexpr int min_blocks = 4;
+    __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog_impl<true, false>(a, b, z0, z1); }
+};
+struct OpLog1pP {
+    static constexpr double dummy = 0.0;
+    static constexpr int min_blocks = 4;
+    __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1p_impl<false>(a, b, z0, z1); }
+};
 struct OpAdd {
     __device__ static void eval(double a, double b, double c, double d, double& z0, double& z1) {
         tf::tadd1(a, b, c, d, z0, z1);
@@ -294,6 +348,30 @@ int tf_tlog(const double* y0, const double* y1, double* z0, double* z1, int64_t 
 }
 int tf_tlog1p(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream) {
     return run_unary<OpLog1p>(y0, y1, z0, z1, n, stream);
+}
+int tf_pexp(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpPExp>(x0, x1, z0, z1, n, stream);
+}
+int tf_pexpm1(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpPExpm1>(x0, x1, z0, z1, n, stream);
+}
+int tf_plog(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpPLog>(y0, y1, z0, z1, n, stream);
+}
+int tf_plog1p(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpPLog1p>(y0, y1, z0, z1, n, stream);
+}
+int tf_texpp(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpExpP>(x0, x1, z0, z1, n, stream);
+}
+int tf_texpm1p(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpExpm1P>(x0, x1, z0, z1, n, stream);
+}
+int tf_tlogp(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpLogP>(y0, y1, z0, z1, n, stream);
+}
+int tf_tlog1pp(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpLog1pP>(y0, y1, z0, z1, n, stream);
 }
 int tf_tadd(const double* x0, const double* x1, const double* y0, const double* y1, double* z0, double* z1,
             int64_t n, void* stream) {

@@ -18,6 +18,8 @@ _lock = threading.Lock()
 
 UNARY = ("texp", "texpm1", "tlog", "tlog1p")
 BINARY = ("tadd", "tmul")
+# Coupled results (p...) and twofold results of coupled arguments (t...p).
+COUPLED = ("pexp", "pexpm1", "plog", "plog1p", "texpp", "texpm1p", "tlogp", "tlog1pp")
 
 
 class TwofoldError(RuntimeError):
@@ -45,6 +47,10 @@ def load(path: str | None = None):
             f.restype = i32
         for name in UNARY:
             f = getattr(lib, "tf_" + name + "f")
+            f.argtypes = [vp, vp, vp, vp, i64, vp]
+            f.restype = i32
+        for name in COUPLED:
+            f = getattr(lib, "tf_" + name)
             f.argtypes = [vp, vp, vp, vp, i64, vp]
             f.restype = i32
         for name in BINARY:
@@ -178,6 +184,53 @@ def tlog1pf(y0, y1=None, out=None, stream=None):
 
 
 FUNCS_F = {"texp": texpf, "texpm1": texpm1f, "tlog": tlogf, "tlog1p": tlog1pf}
+
+
+def pexp(x0, x1=None, out=None, stream=None):
+    """Coupled (z0, z1): z0 + z1 = e^(x0 + x1) with z0 = RN(z0 + z1)."""
+    return _unary("pexp", x0, x1, out, stream)
+
+
+def pexpm1(x0, x1=None, out=None, stream=None):
+    """Coupled (z0, z1): z0 + z1 = e^(x0 + x1) - 1 with z0 = RN(z0 + z1)."""
+    return _unary("pexpm1", x0, x1, out, stream)
+
+
+def plog(y0, y1=None, out=None, stream=None):
+    """Coupled (z0, z1): z0 + z1 = log(y0 + y1) with z0 = RN(z0 + z1)."""
+    return _unary("plog", y0, y1, out, stream)
+
+
+def plog1p(y0, y1=None, out=None, stream=None):
+    """Coupled (z0, z1): z0 + z1 = log(1 + y0 + y1) with z0 = RN(z0 + z1)."""
+    return _unary("plog1p", y0, y1, out, stream)
+
+
+def texpp(x0, x1=None, out=None, stream=None):
+    """As texp for a coupled argument (no renormalising path for a loose x1)."""
+    return _unary("texpp", x0, x1, out, stream)
+
+
+def texpm1p(x0, x1=None, out=None, stream=None):
+    """As texpm1 for a coupled argument."""
+    return _unary("texpm1p", x0, x1, out, stream)
+
+
+def tlogp(y0, y1=None, out=None, stream=None):
+    """As tlog for a coupled argument."""
+    return _unary("tlogp", y0, y1, out, stream)
+
+
+def tlog1pp(y0, y1=None, out=None, stream=None):
+    """As tlog1p for a coupled argument."""
+    return _unary("tlog1pp", y0, y1, out, stream)
+
+
+FUNCS_C = {"pexp": pexp, "pexpm1": pexpm1, "plog": plog, "plog1p": plog1p,
+           "texpp": texpp, "texpm1p": texpm1p, "tlogp": tlogp, "tlog1pp": tlog1pp}
+# the twofold function each one is built on
+BASE_OF = {"pexp": "texp", "pexpm1": "texpm1", "plog": "tlog", "plog1p": "tlog1p",
+           "texpp": "texp", "texpm1p": "texpm1", "tlogp": "tlog", "tlog1pp": "tlog1p"}
 
 
 # operation codes of the chain entry points (TF_OP_* in include/tf.h)

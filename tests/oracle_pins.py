@@ -459,6 +459,41 @@ def pin_chain_condition(lib):
     return fails
 
 
+@_hiprec
+def pin_coupled_decimal(lib):
+    """oracle.coupled: Z0 is RN(f(x0 + x1)) with f evaluated in decimal from the
+    exact sum x0 + x1, Gh + Gl the remainder; for x1 = 0 the answer is
+    unchanged (Z0 = RN(f(x0)) is already the coupled main part)."""
+    fails = []
+    pts = mainpart_points()
+    c = _ctx(80)
+    for func in UNARY:
+        x0 = pts[func]
+        r0 = oracle.evaluate(func, x0, None, lib=lib)
+        c0 = oracle.coupled(r0)
+        same = (c0.Z0 == r0.Z0) | (np.isnan(c0.Z0) & np.isnan(r0.Z0))
+        if not np.all(same):
+            fails.append(f"{func}: coupled changed Z0 of a dotted argument at {np.nonzero(~same)[0][:3]}")
+        for scale, seed in ((2.0**-53, 150), (2.0**-30, 151)):
+            x1 = x0 * (2 * _u(seed, x0.shape[0]) - 1) * scale
+            r = oracle.coupled(oracle.evaluate(func, x0, x1, lib=lib))
+            for i in range(x0.shape[0]):
+                if r.flags[i] & oracle.FL_EXACT:
+                    continue
+                d = c.add(_D(x0[i]), _D(x1[i]))
+                if func == "tlog" and d <= 0 or func == "tlog1p" and d <= -1:
+                    continue
+                F = dec_eval(func, d, 70)
+                want = oracle.round_to_double(F)
+                if not (r.Z0[i] == want or (math.isinf(want) and r.Z0[i] == want)):
+                    fails.append(f"coupled {func}({x0[i]!r}+{x1[i]!r}): Z0={r.Z0[i]!r} decimal={want!r}")
+                    continue
+                if math.isfinite(want) and not _close(r.Gh[i], r.Gl[i], c.subtract(F, _D(want)), F):
+                    fails.append(f"coupled {func}({x0[i]!r}+{x1[i]!r}): remainder {r.Gh[i]!r}+{r.Gl[i]!r}")
+    return fails
+
+
 ALL_PINS = [pin_mainpart_decimal, pin_deviation_decimal, pin_closed_forms, pin_series,
             pin_invariants, pin_special, pin_arith, pin_cancellation, pin_chain_decimal,
-            pin_chain_condition, pin_mainpart_decimal_f32, pin_deviation_decimal_f32]
+            pin_chain_condition, pin_mainpart_decimal_f32, pin_deviation_decimal_f32,
+            pin_coupled_decimal]
