@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--no-chains", action="store_true", help="skip the batched-chains measurement")
     ap.add_argument("--no-tier", action="store_true", help="skip the float/double precision-tier measurement")
     ap.add_argument("--no-coupled", action="store_true",
-                    help="skip the coupled-result / coupled-argument variants (pexp ... tlog1pp)")
+                    help="skip the variant entry points (pexp ... tlog1pp, texp_tables)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the size sweep")
     ap.add_argument("--tier-log2n", type=int, default=28)
     ap.add_argument("--sweep-max", type=int, default=26, choices=(26, 28, 30),
@@ -289,7 +289,8 @@ def _time_launches(fn, reps=5, warm=3):
 
 def coupled_variants(dev, dargs, n, reps=5):
     """Kernel time of the coupled-result (pexp, pexpm1, plog, plog1p) and
-    coupled-argument (texpp, texpm1p, tlogp, tlog1pp) entry points on the same
+    coupled-argument (texpp, texpm1p, tlogp, tlog1pp) entry points, and of
+    texp through the paper's own table reduction (texp_tables), on the same
     inputs as their twofold functions, CUDA events, mean of ``reps`` launches
     after one warm-up."""
     import torch
@@ -312,6 +313,20 @@ def coupled_variants(dev, dargs, n, reps=5):
             res[key] = e0.elapsed_time(e1) / reps
         out[name] = {"ms": res[name], "gelem_s": n / (res[name] * 1e-3) / 1e9, "twofold": base,
                      "twofold_ms": res[base], "time_ratio": res[name] / res[base]}
+    # A/B: texp through the paper's own table reduction (same inputs)
+    res = {}
+    for key, f in (("texp_tables", tf.texp_tables), ("texp", tf.texp)):
+        f(*dargs["texp"], out=(z0, z1), stream=st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            f(*dargs["texp"], out=(z0, z1), stream=st)
+        e1.record(st)
+        e1.synchronize()
+        res[key] = e0.elapsed_time(e1) / reps
+    out["texp_tables"] = {"ms": res["texp_tables"], "gelem_s": n / (res["texp_tables"] * 1e-3) / 1e9,
+                          "twofold": "texp", "twofold_ms": res["texp"], "time_ratio": res["texp_tables"] / res["texp"],
+                          "what": "the paper's own reduction x = 2m + n/256 + y (K = 8, L = 1), tables e^(2m), e^(n/256)"}
     return out
 
 
@@ -527,7 +542,7 @@ def ours(a, world, rank, local):
                    "l2": "no flush: every input array (512 MiB) is larger than L2", "parallelism": f"dp{world}"},
         "roofline": roof, "per_func": per, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": len(FUNCS) * a.steps, "clocks": ck, "chains": chain, "precision_tier": tier,
-        "size_sweep": sweep, "coupled_variants": coupled,
+        "size_sweep": sweep, "variants": coupled,
     }), flush=True)
 
 

@@ -111,6 +111,15 @@ int tf_texpm1p(const double* x0, const double* x1, double* z0, double* z1, int64
 int tf_tlogp(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
 int tf_tlog1pp(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
 
+/* tf_texp computed with the paper's own argument reduction instead (an A/B
+ * variant).  Paper: "Function pexp0()": x = 2^L m + 2^-K n + y with y exact and
+ * e^x = E C e^y, E = e^(2^L m) and C = e^(n/2^K) from tables; here K = 8 and
+ * L = 1 (|y| <= 2^-9, so the Taylor part is the same as tf_texp's), the tables
+ * e^(2m) and e^(n/256) in 128-bit fixed point.  Same results contract as
+ * tf_texp (z0 = RN(e^x0), z0 + z1 within the same bound; z1 may differ from
+ * tf_texp's in its last bits). */
+int tf_texp_tables(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream);
+
 /* Float twofolds: the same four functions over pairs of floats, with the
  * paper's "f"-suffixed float variants in mind ("Twofold exponent" and
  * "Twofold logarithm" give each algorithm for float and double).  Every

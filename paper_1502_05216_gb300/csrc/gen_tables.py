@@ -32,6 +32,11 @@ nearest, each with its unit):
       bits of c_i as a double} with c_i = C_i 2^-24, C_i = round(2^34 / i): the
       reciprocal table of the logarithm, log z = -log c_i + log1p(t) with
       t = z c_i - 1 exact and |t| < 2^-10.4.
+  TF_PX_C[n], TF_PX_E[m]  the tables of the paper's own reduction (Function
+      pexp0(): x = 2^L m + 2^-K n + y, y exact), with K = 8 and L = 1:
+      TF_PX_C[n] = e^(n/256), n = -511 .. 511, units 2^-124 as (lo64, hi64);
+      TF_PX_E[m] = e^(2m) = E_m 2^e_m, m = -373 .. 373, as {lo64, hi64, e_m, 0}
+      with E_m in [2^127, 2^128) (rounded to nearest).
   TF_LG_m      (-1)^m / (m+1), m = 0 .. 5, units 2^-62 (two's complement): the
       coefficients of log1p(t)/t.
 """
@@ -162,6 +167,32 @@ def main(out=sys.stdout):
         assert D(cd) == c
         Lu = L & (2**128 - 1)
         w(f"  {{0x{Lu & (2**64 - 1):016x}ull, 0x{Lu >> 64:016x}ull, {C}ull, 0x{struct.unpack('<Q', struct.pack('<d', cd))[0]:016x}ull}},\n")
+    w("};\n\n")
+    # the paper's reduction: K = 8, L = 1
+    w("#define TF_PX_CHALF 511\n#define TF_PX_EHALF 373\n")
+    w("/* e^(n/256) in units 2^-124 as {lo64, hi64}; index n + 511 */\n")
+    w("TF_TABLE_QUALIFIER unsigned long long TF_PX_C[1023][2] = {\n")
+    for n in range(-511, 512):
+        v = CTX.exp(CTX.divide(D(n), 256))
+        x = fixed(v, 124)
+        assert 0 < x < 2**127
+        w(f"  {{{u128(x)}}},\n")
+    w("};\n")
+    w("/* e^(2m) = E 2^e, E in [2^127, 2^128), as {lo64, hi64, e, 0}; index m + 373 */\n")
+    w("TF_TABLE_QUALIFIER unsigned long long TF_PX_E[747][4] = {\n")
+    for m in range(-373, 374):
+        v = CTX.exp(D(2 * m))
+        e = int(CTX.log10(v) / CTX.log10(D(2)))  # approximate exponent, corrected below
+        while CTX.power(D(2), e) > v:
+            e -= 1
+        while CTX.power(D(2), e + 1) <= v:
+            e += 1
+        x = fixed(CTX.multiply(v, CTX.power(D(2), -e)), 127)
+        ee = e - 127
+        if x == 2**128:
+            x, ee = 2**127, ee + 1
+        assert 2**127 <= x < 2**128
+        w(f"  {{{u128(x)}, 0x{ee & (2**64 - 1):016x}ull, 0ull}},\n")
     w("};\n\n")
     w("/* 2^(j/256) in units of 2^-127 as {lo64, hi64}; index j + 128 */\n")
     w("TF_TABLE_QUALIFIER unsigned long long TF_TFIX_TABLE[257][2] = {\n")

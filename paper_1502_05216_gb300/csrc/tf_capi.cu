@@ -92,6 +92,11 @@ struct OpLog1pP {
     static constexpr int min_blocks = 4;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1p_impl<false>(a, b, z0, z1); }
 };
+struct OpExpTables {
+    static constexpr double dummy = 0.0;
+    static constexpr int min_blocks = 4;
+    __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp_impl<true, true, true>(a, b, z0, z1); }
+};
 struct OpAdd {
     __device__ static void eval(double a, double b, double c, double d, double& z0, double& z1) {
         tf::tadd1(a, b, c, d, z0, z1);
@@ -372,6 +377,9 @@ int tf_tlogp(const double* y0, const double* y1, double* z0, double* z1, int64_t
 }
 int tf_tlog1pp(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream) {
     return run_unary<OpLog1pP>(y0, y1, z0, z1, n, stream);
+}
+int tf_texp_tables(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpExpTables>(x0, x1, z0, z1, n, stream);
 }
 int tf_tadd(const double* x0, const double* x1, const double* y0, const double* y1, double* z0, double* z1,
             int64_t n, void* stream) {

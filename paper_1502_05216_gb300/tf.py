@@ -20,6 +20,8 @@ UNARY = ("texp", "texpm1", "tlog", "tlog1p")
 BINARY = ("tadd", "tmul")
 # Coupled results (p...) and twofold results of coupled arguments (t...p).
 COUPLED = ("pexp", "pexpm1", "plog", "plog1p", "texpp", "texpm1p", "tlogp", "tlog1pp")
+# the same function computed another way (the paper's own exp reduction)
+VARIANTS = ("texp_tables",)
 
 
 class TwofoldError(RuntimeError):
@@ -49,7 +51,7 @@ def load(path: str | None = None):
             f = getattr(lib, "tf_" + name + "f")
             f.argtypes = [vp, vp, vp, vp, i64, vp]
             f.restype = i32
-        for name in COUPLED:
+        for name in COUPLED + VARIANTS:
             f = getattr(lib, "tf_" + name)
             f.argtypes = [vp, vp, vp, vp, i64, vp]
             f.restype = i32
@@ -224,6 +226,11 @@ def tlogp(y0, y1=None, out=None, stream=None):
 def tlog1pp(y0, y1=None, out=None, stream=None):
     """As tlog1p for a coupled argument."""
     return _unary("tlog1pp", y0, y1, out, stream)
+
+
+def texp_tables(x0, x1=None, out=None, stream=None):
+    """texp computed with the paper's own table reduction (A/B variant)."""
+    return _unary("texp_tables", x0, x1, out, stream)
 
 
 FUNCS_C = {"pexp": pexp, "pexpm1": pexpm1, "plog": plog, "plog1p": plog1p,
