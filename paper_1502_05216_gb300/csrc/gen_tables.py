@@ -15,6 +15,9 @@ Float twofold (float-float on the FP32 pipes) constants:
   TF_F_L0..L2  ln2 = L0 + L1 + L2, L0 with 16 significant bits (n*L0 exact for
       |n| < 2^8), L1, L2 floats.
   TF_F_R3..R5  1/3! .. 1/5! rounded to float (the dotted Taylor tail).
+  TF_FLOGT[i] for i = 1448 .. 2896: {c_i, -log c_i as (hi, lo) floats, c_i - 1}
+      with c_i = RN_float(2048 / i): the reciprocal table of the float
+      logarithm, log z = -log c_i + log1p(z c_i - 1), |z c_i - 1| < 2^-11.4.
   TF_FT[j], TF_FE[j]  2^(j/256) and 2^(j/256) - 1 as (hi, lo) floats, j = -128 .. 128.
 
 Fixed-point constants of the integer exp core (unsigned integers, rounded to
@@ -114,6 +117,20 @@ def main(out=sys.stdout):
     w(f"#define TF_F_L0 {hexf(FL0)}\n#define TF_F_L1 {hexf(FL1)}\n#define TF_F_L2 {hexf(FL2)}\n")
     for m in range(3, 6):
         w(f"#define TF_F_R{m} {hexf(f32_nearest(CTX.divide(1, D(math.factorial(m)))))}\n")
+    w("#define TF_FLOGT_LO 1448\n#define TF_FLOGT_HI 2896\n")
+    w("/* {c_i, -log c_i hi, lo, c_i - 1} floats, c_i = RN_float(2048 / i), i = 1448 .. 2896 */\n")
+    w("TF_TABLE_QUALIFIER float TF_FLOGT[1449][4] = {\n")
+    for i in range(1448, 2897):
+        cf = f32_nearest(CTX.divide(D(2048), D(i)))
+        L = CTX.minus(CTX.ln(D(cf)))
+        h, l = fsplit_exact(L, 2)
+        cm1 = CTX.subtract(D(cf), 1)
+        assert D(f32_nearest(cm1)) == cm1  # c - 1 exact in float (Sterbenz)
+        z_lo, z_hi = D(i) / 2048 - D(1) / 4096, D(i) / 2048 + D(1) / 4096
+        for zz in (max(z_lo, D("0.70710678")), min(z_hi, D("1.41421357"))):
+            assert abs(CTX.subtract(CTX.multiply(zz, D(cf)), 1)) < D(2) ** D("-11.4"), (i, zz)
+        w(f"  {{{hexf(cf)}, {hexf(h)}, {hexf(l)}, {hexf(f32_nearest(cm1))}}},\n")
+    w("};\n")
     for name, minus1 in (("TF_FT", False), ("TF_FE", True)):
         w(f"/* {'2^(j/256) - 1' if minus1 else '2^(j/256)'} as (hi, lo) floats; index j + 128 */\n")
         w(f"TF_TABLE_QUALIFIER float {name}_TABLE[257][2] = {{\n")

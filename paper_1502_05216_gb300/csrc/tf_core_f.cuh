@@ -13,10 +13,12 @@
 //              so the tail's rounding stays below 2^-55 and e^x - 1 keeps
 //              2^-45 relative where E_j + T_j P cancels);
 //              e^x = 2^k T_j (1 + P),  e^x - 1 = 2^k (E_j + T_j P) + 2^k - 1
-//   log        y = 2^n z, z in [sqrt(1/2), sqrt(2)), d = z - 1 exact; seed
-//              r0 = log1pf(d) (1x float); one Newton step on e^x - 1 with the
-//              float-float exp core: u = d + S + d S, S = e^-r0 - 1;
-//              log y = n ln2 + r0 + u - u^2/2 (paper, "Newton inversion")
+//   log        y = 2^n z, z in [sqrt(1/2), sqrt(2)), d = z - 1 exact; a
+//              reciprocal table reduces z to t = z c_i - 1 (exact pair,
+//              |t| < 2^-11.4); seed R ~ log1p(t) (1x float); one Newton step
+//              on e^x: u = t + S + t S, S = e^-R - 1 (a short float-float
+//              series); log y = n ln2 - log c_i + R + u (paper, "Newton
+//              inversion")
 //
 // z0 = RN_float(f(x0)) from the float-float value (2^-46 or better), so it is
 // correctly rounded unless f(x0) lies that close to a rounding midpoint; the
@@ -342,27 +344,49 @@ __device__ __forceinline__ void texpm1f_impl(float x0, float x1, float& z0, floa
 }
 
 // ---------------------------------------------------------------------------
-// Logarithm over float.  log_newton_f: n ln2 + log(1 + d), d = dh + dl.
-// u = (1 + d)(1 + S) - 1 is formed as a float-float pair (the 1x float seed
-// leaves |u| ~ 2^-23 |r0|, so one float would cost 2^-46); log1p(u) = u - u^2/2.
+// Logarithm over float (paper, "Newton inversion"), after a reciprocal-table
+// reduction as in the double path.  z = 1 + d in [sqrt(1/2), sqrt(2)),
+// i = round(2048 z), c = c_i from TF_FLOGT (the float nearest 2048/i):
+//   log z = -log c + log1p(t),   t = (c - 1) + d c = th + tl exactly
+// (d c split by an FMA; (c - 1) plus its high part cancels exactly by the
+// Sterbenz lemma, or c = 1), |t| < 2^-11.4.  Seed R = t - t^2/2 + t^3/3 in
+// float (within about 2^-24 |t|); one Newton step on e^x:
+//   S = e^-R - 1 = -R + R^2/2 - R^3/6 + R^4/24 - R^5/120 as a float pair,
+//   u = (1 + t)(1 + S) - 1 = t + S + t S   (t + S and t S cancel exactly),
+//   log1p(t) = R + u (u^2/2 is below 2^-48 |t|).
+// Then n ln2 (L0 + L1 + L2, n L0 exact) - log c (a float pair) + R + u.
+// Also S0 = 1/z - 1 to 1x (c (1 + S) - 1), for the x1 term.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ ff log_newton_f(float dh, float dl, int n, float& S0) {
-    float r0 = log1pf(add(dh, dl));  // seed, 1x float, |r0| <= 0.3466
-    ff S = expm1_small_f(-r0);
-    ff p = two_prod(dh, S.hi);
-    ff a = two_sum(dh, S.hi);
-    ff b = two_sum(a.hi, p.hi);
-    float ul = add(add(add(a.lo, b.lo), p.lo), add(fma_rn(dh, S.lo, S.lo), fma_rn(dl, S.hi, dl)));
-    ff u = fast_two_sum(b.hi, ul);
-    float ql = fma_rn(mul(-0.5f, u.hi), u.hi, u.lo);
-    ff R = fast_two_sum(r0, u.hi);  // |u| << |r0| (or both 0)
-    R.lo = add(R.lo, ql);
+    const float kShift = 0x1.8p23f;
+    float kf = fma_rn(dh, 2048.0f, kShift);  // |2048 d| < 849: round(2048 d) in the low bits
+    int i = 2048 + (int)(bits(kf) - bits(kShift));
+    i = min(max(i, TF_FLOGT_LO), TF_FLOGT_HI);
+    float4 T = __ldg(reinterpret_cast<const float4*>(TF_FLOGT) + (i - TF_FLOGT_LO));
+    const float c = T.x, Lh = T.y, Ll = T.z, cm1 = T.w;
+    ff p = two_prod(dh, c);
+    float th = add(cm1, p.hi);               // exact
+    float tl = fma_rn(dl, c, p.lo);
+    // seed
+    float R = fma_rn(mul(th, th), fma_rn(th, 0x1.555556p-2f, -0.5f), th);
+    // S = e^-R - 1
+    ff q = two_prod(R, R);
+    float tail = mul(mul(q.hi, R), fma_rn(fma_rn(R, -0x1.111112p-7f, 0x1.555556p-5f), R, -0x1.555556p-3f));
+    ff Sh = fast_two_sum(-R, mul(0.5f, q.hi));
+    float Sl = add(Sh.lo, fma_rn(0.5f, q.lo, tail));
+    // u = t + S + t S
+    ff a = two_sum(th, Sh.hi);
+    ff m = two_prod(th, Sh.hi);
+    float small = add(add(a.lo, m.lo), add(add(Sl, tl), fma_rn(tl, Sh.hi, mul(th, Sl))));
+    float u = add(add(a.hi, m.hi), small);  // a.hi + m.hi exact (opposite, within a factor 2)
+    // n ln2 - log c + R + u
+    ff s1 = two_sum(Lh, R);
     float nf = (float)n;
-    ff a2 = fast_two_sum(mul(nf, TF_F_L0), R.hi);  // n L0 exact; |n L0| >= 0.69 > |R| or n = 0
+    ff s2 = fast_two_sum(mul(nf, TF_F_L0), s1.hi);  // n L0 exact; |n L0| >= 0.69 or n = 0
     ff b2 = two_prod(nf, TF_F_L1);
-    ff c2 = two_sum(a2.hi, b2.hi);
-    float lo = add(add(add(a2.lo, c2.lo), add(b2.lo, mul(nf, TF_F_L2))), R.lo);
-    S0 = S.hi;
+    ff c2 = two_sum(s2.hi, b2.hi);
+    float lo = add(add(add(s2.lo, c2.lo), fma_rn(nf, TF_F_L2, b2.lo)), add(add(s1.lo, Ll), u));
+    S0 = fma_rn(c, Sh.hi, cm1);
     return fast_two_sum(c2.hi, lo);
 }
 
