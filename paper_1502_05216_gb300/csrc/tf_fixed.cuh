@@ -139,11 +139,19 @@ __device__ __forceinline__ u128 mul53_top(uint64_t m, u128 b) {
 // M 2^E| <= 2^-115 |hi|.  M == 0 gives (+-0, 0).  The caller guarantees that
 // both parts are normal doubles (2^-960 <= M 2^E < 2^1023).
 // ---------------------------------------------------------------------------
+template <bool kHi = false>
 __device__ __forceinline__ void to_pair(u128 M, int E, bool neg, double& hi, double& lo) {
     const uint64_t sgn = neg ? 0x8000000000000000ull : 0ull;
     bool zero = (M.hi | M.lo) == 0;
-    int lz = (M.hi != 0) ? __clzll((long long)M.hi) : 64 + __clzll((long long)(M.lo | 1ull));
-    u128 Mn = shl128_var(M, lz);  // bit 127 set
+    int lz;
+    u128 Mn;
+    if constexpr (kHi) {  // the caller guarantees M.hi != 0: a one-word count and shift
+        lz = min(__clzll((long long)M.hi), 63);
+        Mn = {M.lo << lz, (M.hi << lz) | ((M.lo >> 1) >> (63 - lz))};
+    } else {
+        lz = (M.hi != 0) ? __clzll((long long)M.hi) : 64 + __clzll((long long)(M.lo | 1ull));
+        Mn = shl128_var(M, lz);  // bit 127 set
+    }
     int L = 127 - lz;              // position of the leading bit of M
     uint64_t m53 = Mn.hi >> 11;
     bool rb = (Mn.hi >> 10) & 1;
