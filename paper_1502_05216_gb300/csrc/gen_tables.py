@@ -9,16 +9,16 @@ All values come from Python's decimal module at 120 significant digits.
   TF_INV_C  256/ln2 rounded to double.
 
 Float twofold (float-float on the FP32 pipes) constants:
-  TF_F_INV_C   256/ln2 rounded to float.
-  TF_F_C0..C2  ln2/256 = C0 + C1 + C2, C0 with 8 significant bits (N*C0 exact
-      for |N| < 2^16), C1, C2 floats (rounded to nearest).
+  TF_F_INV_C   512/ln2 rounded to float.
+  TF_F_C0..C2  ln2/512 = C0 + C1 + C2, C0 with 7 significant bits (N*C0 exact
+      for |N| < 2^17), C1, C2 floats (rounded to nearest).
   TF_F_L0..L2  ln2 = L0 + L1 + L2, L0 with 16 significant bits (n*L0 exact for
       |n| < 2^8), L1, L2 floats.
   TF_F_R3..R5  1/3! .. 1/5! rounded to float (the dotted Taylor tail).
   TF_FLOGT[i] for i = 1448 .. 2896: {c_i, -log c_i as (hi, lo) floats, c_i - 1}
       with c_i = RN_float(2048 / i): the reciprocal table of the float
       logarithm, log z = -log c_i + log1p(z c_i - 1), |z c_i - 1| < 2^-11.4.
-  TF_FT[j], TF_FE[j]  2^(j/256) and 2^(j/256) - 1 as (hi, lo) floats, j = -128 .. 128.
+  TF_FT[j], TF_FE[j]  2^(j/512) and 2^(j/512) - 1 as (hi, lo) floats, j = -256 .. 256.
 
 Fixed-point constants of the integer exp core (unsigned integers, rounded to
 nearest, each with its unit):
@@ -106,13 +106,13 @@ def main(out=sys.stdout):
     w(f"#define TF_C0 {hexd(C0)}\n")
     w("\n")
     # float twofold constants
-    cf = CTX.divide(ln2, 256)
-    FC0 = trunc_bits(cf, 8)
+    cf = CTX.divide(ln2, 512)
+    FC0 = trunc_bits(cf, 7)
     FC1, FC2 = fsplit_exact(CTX.subtract(cf, D(FC0)), 2)
     FL0 = trunc_bits(ln2, 16)
     FL1, FL2 = fsplit_exact(CTX.subtract(ln2, D(FL0)), 2)
     w("/* float twofold path */\n")
-    w(f"#define TF_F_TAB_HALF 128\n#define TF_F_INV_C {hexf(f32_nearest(CTX.divide(256, ln2)))}\n")
+    w(f"#define TF_F_TAB_HALF 256\n#define TF_F_INV_C {hexf(f32_nearest(CTX.divide(512, ln2)))}\n")
     w(f"#define TF_F_C0 {hexf(FC0)}\n#define TF_F_C1 {hexf(FC1)}\n#define TF_F_C2 {hexf(FC2)}\n")
     w(f"#define TF_F_L0 {hexf(FL0)}\n#define TF_F_L1 {hexf(FL1)}\n#define TF_F_L2 {hexf(FL2)}\n")
     for m in range(3, 6):
@@ -132,10 +132,10 @@ def main(out=sys.stdout):
         w(f"  {{{hexf(cf)}, {hexf(h)}, {hexf(l)}, {hexf(f32_nearest(cm1))}}},\n")
     w("};\n")
     for name, minus1 in (("TF_FT", False), ("TF_FE", True)):
-        w(f"/* {'2^(j/256) - 1' if minus1 else '2^(j/256)'} as (hi, lo) floats; index j + 128 */\n")
-        w(f"TF_TABLE_QUALIFIER float {name}_TABLE[257][2] = {{\n")
-        for j in range(-128, 129):
-            v = CTX.power(D(2), CTX.divide(D(j), 256))
+        w(f"/* {'2^(j/512) - 1' if minus1 else '2^(j/512)'} as (hi, lo) floats; index j + 256 */\n")
+        w(f"TF_TABLE_QUALIFIER float {name}_TABLE[513][2] = {{\n")
+        for j in range(-256, 257):
+            v = CTX.power(D(2), CTX.divide(D(j), 512))
             if minus1:
                 v = CTX.subtract(v, 1)
             h, l = fsplit_exact(v, 2)

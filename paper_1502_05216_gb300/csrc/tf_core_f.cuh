@@ -6,10 +6,10 @@
 // on the FP32 pipes (paper, "Method summary": twofold partial sums with
 // 1x-precise coefficients; TwoSum / FMA-based TwoProduct in float):
 //
-//   exp core   x = N ln2/256 + r, N = 256 k + j, r = rh + rl (ln2/256 in three
-//              floats, the first of 8 bits so that N C0 is exact);
+//   exp core   x = N ln2/512 + r, N = 512 k + j, r = rh + rl (ln2/512 in three
+//              floats, the first of 7 bits so that N C0 is exact);
 //              e^r - 1 = rh + rh^2/2 + rh^3 q(rh) + rl (1 + rh), the first two
-//              terms in float-float, the dotted tail q in float (|r| < 2^-9.5,
+//              terms in float-float, the dotted tail q in float (|r| < 2^-10.5,
 //              so the tail's rounding stays below 2^-55 and e^x - 1 keeps
 //              2^-45 relative where E_j + T_j P cancels);
 //              e^x = 2^k T_j (1 + P),  e^x - 1 = 2^k (E_j + T_j P) + 2^k - 1
@@ -85,8 +85,9 @@ __device__ __forceinline__ ff tab(const float (*t)[2], int j) {
 }
 
 // ---------------------------------------------------------------------------
-// exp core.  r = rh + rl to ~2^-57 absolute for |N| <= 128 (2^-49 at the
-// largest N); P = e^r - 1 as Ph + Pl to ~2^-55.
+// exp core.  r = rh + rl to ~2^-57 absolute for |N| <= 256 (2^-48 at the
+// largest N); P = e^r - 1 as Ph + Pl to ~2^-57 (|r| < 2^-10.5: the cubic tail
+// rh^3 q, rounded in float, stays below 2^-34).
 // ---------------------------------------------------------------------------
 struct RedF {
     float rh, rl;
@@ -95,10 +96,10 @@ struct RedF {
 
 __device__ __forceinline__ RedF reduce_f(float x) {
     const float kShift = 0x1.8p23f;
-    float t = fma_rn(x, TF_F_INV_C, kShift);  // |x 256/ln2| < 2^22: N in the low bits
+    float t = fma_rn(x, TF_F_INV_C, kShift);  // |x 512/ln2| < 2^22: N in the low bits
     int N = (int)(bits(t) - bits(kShift));
     float Nf = sub(t, kShift);
-    float r0 = fma_rn(-Nf, TF_F_C0, x);  // exact: N C0 has at most 24 bits (|N| < 2^16)
+    float r0 = fma_rn(-Nf, TF_F_C0, x);  // exact: N C0 has at most 24 bits (|N| < 2^17)
     ff p1 = two_prod(Nf, TF_F_C1);
     ff r = two_sum(r0, -p1.hi);
     float rl = fma_rn(-Nf, TF_F_C2, sub(r.lo, p1.lo));
@@ -129,8 +130,8 @@ struct ExpCoreF {
 
 __device__ __forceinline__ ExpCoreF exp_core_f(float x) {
     RedF R = reduce_f(x);
-    int k = (R.N + TF_F_TAB_HALF) >> 8;
-    int j = R.N - (k << 8);
+    int k = (R.N + TF_F_TAB_HALF) >> 9;
+    int j = R.N - (k << 9);
     ff P = expm1_reduced_f(R.rh, R.rl);
     ff T = tab(TF_FT_TABLE, j);
     ff m = tab_times_f(T, P);
@@ -140,8 +141,8 @@ __device__ __forceinline__ ExpCoreF exp_core_f(float x) {
     return {z.hi, z.lo, k};
 }
 
-// e^x - 1 for |x| <= 0.3466 (k = 0, j = N in [-128, 128]) as a renormalised pair:
-// E_j + T_j P (|E_j| >= 0.0027 > |T_j P|), or P itself for N = 0 (r = x exactly,
+// e^x - 1 for |x| <= 0.3466 (k = 0, j = N in [-256, 256]) as a renormalised pair:
+// E_j + T_j P (|E_j| >= 0.00135 > |T_j P|), or P itself for N = 0 (r = x exactly,
 // so the relative precision holds down to tiny x).
 __device__ __forceinline__ ff expm1_small_f(float x) {
     RedF R = reduce_f(x);
@@ -301,9 +302,9 @@ template <bool kVote, bool kTop>
 __device__ __forceinline__ void texpm1f_impl(float x0, float x1, float& z0, float& z1) {
     float x = clamp_exp_arg(x0);
     RedF R = reduce_f(x);
-    int k = (R.N + TF_F_TAB_HALF) >> 8;
+    int k = (R.N + TF_F_TAB_HALF) >> 9;
     k = (R.N == TF_F_TAB_HALF) ? 0 : k;
-    int j = R.N - (k << 8);
+    int j = R.N - (k << 9);
     ff P = expm1_reduced_f(R.rh, R.rl);
     ff T = tab(TF_FT_TABLE, j);
     ff E = tab(TF_FE_TABLE, j);
