@@ -165,15 +165,10 @@ __device__ __forceinline__ float clamp_exp_arg(float x) {
     return x;
 }
 
-__device__ __forceinline__ float half_of(float x1) {
-    uint32_t b = bits(x1);
-    return ((b & kExpMask) > (1u << 23)) ? from_bits(b - (1u << 23)) : 0.0f;
-}
-
 // e (x1 + x1^2/2) + c, x1 small (|x1| < 2^-15: the x1^3 term is below 2^-47 |x1|).
 __device__ __forceinline__ float add_pert(float e, float x1, float c) {
     float p = mul(e, x1);
-    return fma_rn(e, x1, fma_rn(p, half_of(x1), c));
+    return fma_rn(e, x1, fma_rn(p, mul(0.5f, x1), c));
 }
 __device__ __forceinline__ bool pert_is_large(float x1) { return absbits(x1) >= 0x38000000u; }  // 2^-15
 __device__ __forceinline__ bool pert_is_loose(float x1) { return absbits(x1) > 0x3eae0000u; }   // 0.33984
@@ -253,7 +248,7 @@ static __device__ __noinline__ void texpf_rare(float x0, float x1, float zA, flo
 template <bool kVote, bool kTop>
 __device__ __forceinline__ void texpf_impl(float x0, float x1, float& z0, float& z1) {
     ExpCoreF c = exp_core_f(clamp_exp_arg(x0));
-    float sk = pow2f(c.k);
+    float sk = from_bits((uint32_t)(c.k + 127) << 23);  // 2^k for -126 <= k <= 127; other k are rare
     z0 = mul(c.zA, sk);
     z1 = mul(add_pert(c.zA, x1, c.eA), sk);  // one rounding into a subnormal z1
     bool rare = (c.k < -125) | (c.k > 127) | pert_is_large(x1);
