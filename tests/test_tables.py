@@ -1,0 +1,143 @@
+"""The committed constant tables of the kernels (csrc/tf_tables.h) against their
+mathematical definitions, recomputed here with Python's decimal module (no GPU).
+
+The build refuses a header that differs from its generator's output; this test
+checks the generator's output itself, entry by entry (every entry of the small
+tables, a stride of the large ones), from the definitions stated in the kernels:
+
+  TF_TFIX_TABLE[j]  2^(j/256) in units 2^-127 (round to nearest)
+  TF_HC_m           1/(m+1)! in units 2^-127 (m <= 4) or 2^-72
+  TF_LN2FIX         ln 2 in units 2^-128;  TF_C0 + TF_C12FIX 2^-148 = ln2/256
+  TF_LG_m           (-1)^m / (m+1) in units 2^-62
+  TF_LOGT[i]        {-log c_i in units 2^-128, C_i = round(2^34 / i), c_i = C_i 2^-24 as a double}
+  TF_PX_C[n]        e^(n/256) in units 2^-124
+  TF_PX_E[m]        e^(2m) = E 2^e, E in [2^127, 2^128)
+  TF_FLOGT[i]       {c = RN_float(2048/i), -log c as a float pair, c - 1}
+  TF_FT / TF_FE[j]  2^(j/512) and 2^(j/512) - 1 as float pairs
+  TF_F_C0..C2       ln2/512 split, C0 with 7 bits;  TF_F_L0..L2  ln 2 split
+"""
+import decimal
+import os
+import re
+import struct
+
+import numpy as np
+
+HDR = os.path.join(os.path.dirname(__file__), "..", "paper_1502_05216_gb300", "csrc", "tf_tables.h")
+D = decimal.Decimal
+C = decimal.Context(prec=70, Emax=99999, Emin=-99999)
+SRC = open(HDR).read()
+LN2 = C.ln(D(2))
+
+
+def _ints(name, width):
+    body = re.search(r"\b%s\[[0-9]+\]\[%d\] = \{(.*?)\};" % (name, width), SRC, re.S).group(1)
+    rows = re.findall(r"\{([^}]*)\}", body)
+    return [[int(v[:-3], 16) if v.startswith("0x") else int(v[:-3]) for v in (x.strip() for x in r.split(","))]
+            for r in rows]
+
+
+def _floats(name, width):
+    body = re.search(r"\b%s\[[0-9]+\]\[%d\] = \{(.*?)\};" % (name, width), SRC, re.S).group(1)
+    rows = re.findall(r"\{([^}]*)\}", body)
+    return [[float.fromhex(v.strip().rstrip("f")) for v in r.split(",")] for r in rows]
+
+
+def _define(name):
+    return re.search(r"#define %s (.*)" % name, SRC).group(1).split("/*")[0].strip()
+
+
+def _u128(text):
+    lo, hi = re.findall(r"0x([0-9a-f]+)ull", text)
+    return int(lo, 16) | (int(hi, 16) << 64)
+
+
+def _fx(v, units):
+    """round(v 2^units) as an int, ties to even."""
+    return int(C.multiply(v, C.power(2, units)).to_integral_value(rounding=decimal.ROUND_HALF_EVEN))
+
+
+def _f32(x):
+    return float(np.float32(x))
+
+
+def test_exp_table_and_constants():
+    tab = _ints("TF_TFIX_TABLE", 2)
+    assert len(tab) == 257
+    for j in range(-128, 129):
+        lo, hi = tab[j + 128]
+        assert lo | (hi << 64) == _fx(C.power(2, C.divide(D(j), 256)), 127), j
+    fact = 1
+    for m in range(10):
+        fact *= m + 1
+        v = C.divide(1, D(fact))
+        d = _define(f"TF_HC_{m}")
+        got = _u128(d) if m <= 4 else int(d.rstrip("ul").replace("0x", ""), 16)
+        assert got == _fx(v, 127 if m <= 4 else 72), m
+    assert _u128(_define("TF_LN2FIX")) == _fx(LN2, 128)
+    c0 = D(float.fromhex(_define("TF_C0")))
+    c12 = C.multiply(D(_u128(_define("TF_C12FIX"))), C.power(2, -148))
+    assert abs(C.subtract(C.add(c0, c12), C.divide(LN2, 256))) < C.power(2, -148)
+    assert float.fromhex(_define("TF_INV_C")) == float(C.divide(256, LN2))
+    for m in range(6):
+        v = int(_define(f"TF_LG_{m}").split("0x")[1].rstrip("ul)"), 16)
+        v = v - (1 << 64) if v >> 63 else v
+        assert v == _fx(C.divide(D((-1) ** m), D(m + 1)), 62), m
+
+
+def test_log_table():
+    tab = _ints("TF_LOGT", 4)
+    assert len(tab) == 725
+    for i in range(724, 1449, 7):
+        lo, hi, Ci, cbits = tab[i - 724]
+        assert Ci == int(C.divide(D(2) ** 34, D(i)).to_integral_value(rounding=decimal.ROUND_HALF_EVEN))
+        c = C.multiply(D(Ci), C.power(2, -24))
+        assert D(struct.unpack("<d", struct.pack("<Q", cbits))[0]) == c
+        L = lo | (hi << 64)
+        L = L - (1 << 128) if L >> 127 else L
+        assert L == _fx(C.minus(C.ln(c)), 128), i
+        # the reduced argument stays below 2^-10.4 over the cell
+        for z in (D(i) / 1024 - D(1) / 2048, D(i) / 1024 + D(1) / 2048):
+            z = min(max(z, D("0.7071067811865475")), D("1.414213562373095"))
+            assert abs(C.subtract(C.multiply(z, c), 1)) < D(2) ** D("-10.4")
+
+
+def test_paper_reduction_tables():
+    ctab = _ints("TF_PX_C", 2)
+    assert len(ctab) == 1023
+    for n in range(-511, 512, 5):
+        lo, hi = ctab[n + 511]
+        assert lo | (hi << 64) == _fx(C.exp(C.divide(D(n), 256)), 124), n
+    etab = _ints("TF_PX_E", 4)
+    assert len(etab) == 747
+    for m in range(-373, 374, 3):
+        lo, hi, e, _ = etab[m + 373]
+        E = lo | (hi << 64)
+        e = e - (1 << 64) if e >> 63 else e
+        assert (1 << 127) <= E < (1 << 128)
+        v = C.multiply(D(E), C.power(2, e))
+        exact = C.exp(D(2 * m))
+        assert abs(C.divide(C.subtract(v, exact), exact)) < C.power(2, -127), m
+
+
+def test_float_tables():
+    L0, L1, L2 = (float.fromhex(_define(f"TF_F_L{k}").rstrip("f")) for k in range(3))
+    assert abs(C.subtract(D(L0) + D(L1) + D(L2), LN2)) < C.power(2, -68)
+    C0, C1, C2 = (float.fromhex(_define(f"TF_F_C{k}").rstrip("f")) for k in range(3))
+    assert abs(C.subtract(D(C0) + D(C1) + D(C2), C.divide(LN2, 512))) <= C.power(2, -68)  # half an ulp of C2
+    assert (int(D(C0) * D(2) ** 16) == D(C0) * D(2) ** 16) and int(_define("TF_F_TAB_HALF")) == 256
+    for name, minus1 in (("TF_FT_TABLE", False), ("TF_FE_TABLE", True)):
+        tab = _floats(name, 2)
+        assert len(tab) == 513
+        for j in range(-256, 257, 3):
+            h, l = tab[j + 256]
+            v = C.power(2, C.divide(D(j), 512)) - (1 if minus1 else 0)
+            assert h == _f32(v) and abs(C.subtract(D(h) + D(l), v)) <= abs(v) * C.power(2, -47) + C.power(2, -160)
+    tab = _floats("TF_FLOGT", 4)
+    assert len(tab) == 1449
+    for i in range(1448, 2897, 7):
+        c, h, l, cm1 = tab[i - 1448]
+        assert c == _f32(C.divide(2048, D(i)))
+        assert D(cm1) == D(c) - 1
+        L = C.minus(C.ln(D(c)))
+        assert abs(C.subtract(D(h) + D(l), L)) <= abs(L) * C.power(2, -47) + C.power(2, -80)
