@@ -40,7 +40,7 @@ nearest, each with its unit):
       TF_PX_C[n] = e^(n/256), n = -511 .. 511, units 2^-124 as (lo64, hi64);
       TF_PX_E[m] = e^(2m) = E_m 2^e_m, m = -373 .. 373, as {lo64, hi64, e_m, 0}
       with E_m in [2^127, 2^128) (rounded to nearest).
-  TF_LG_m      (-1)^m / (m+1), m = 0 .. 5, units 2^-62 (two's complement): the
+  TF_LG_m      (-1)^m / (m+1), m = 0 .. 4, units 2^-62 (two's complement): the
       coefficients of log1p(t)/t.
 """
 import decimal
@@ -165,7 +165,7 @@ def main(out=sys.stdout):
     w(f"#define TF_C12FIX {{{u128(fixed(c12, 148))}}}\n\n")
     w(f"#define TF_LN2FIX {{{u128(fixed(ln2, 128))}}}\n\n")
     w("/* coefficients (-1)^m/(m+1) of log1p(t)/t, units 2^-62, two's complement */\n")
-    for m in range(0, 6):
+    for m in range(0, 5):
         x = fixed(CTX.divide(D((-1) ** m), D(m + 1)), 62)
         w(f"#define TF_LG_{m} ((long long)0x{x & (2**64 - 1):016x}ull)\n")
     w("\n#define TF_LOGT_LO 724\n#define TF_LOGT_HI 1448\n")

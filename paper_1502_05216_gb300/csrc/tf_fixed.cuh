@@ -35,8 +35,6 @@ __device__ __forceinline__ u128 add128(u128 a, u128 b) { return U(V(a) + V(b)); 
 
 __device__ __forceinline__ u128 sub128(u128 a, u128 b) { return U(V(a) - V(b)); }
 
-__device__ __forceinline__ u128 add128_64(u128 a, uint64_t b) { return U(V(a) + b); }
-
 // Two's complement negation.
 __device__ __forceinline__ u128 neg128(u128 a) { return U(0 - V(a)); }
 
@@ -120,12 +118,10 @@ __device__ __forceinline__ u128 mul128_u32_shr(u128 a, uint32_t n) {
     return U((((v128)a.lo * n) >> s) + (((v128)a.hi * n) << (64 - s)));
 }
 
-// High 64 bits of the signed 128-bit product of two signed 64-bit integers.
-__device__ __forceinline__ int64_t mul_hi_s(int64_t a, int64_t b) {
-    uint64_t h = __umul64hi((uint64_t)a, (uint64_t)b);
-    h -= (a < 0) ? (uint64_t)b : 0ull;
-    h -= (b < 0) ? (uint64_t)a : 0ull;
-    return (int64_t)h;
+// High 64 bits of the signed product of a signed a and a non-negative b < 2^63
+// (one sign correction: for a < 0 the unsigned product is a b + 2^64 b).
+__device__ __forceinline__ int64_t mul_hi_su(int64_t a, uint64_t b) {
+    return (int64_t)(__umul64hi((uint64_t)a, b) - ((a < 0) ? b : 0ull));
 }
 
 // The top 128 bits of the 181-bit product m * b (m < 2^53): (m b) >> 64.
