@@ -251,14 +251,14 @@ CHAIN_WORKLOAD = ("65,536 independent chains, lengths geometric (mean 256, cap 4
 
 
 def chains_bench(dev):
-    """The batched-chains workload: one fused persistent launch (autotuned block
-    size and grid) against one launch per step and op kind, each captured in a
+    """The batched-chains workload: one fused persistent launch (autotuned chains
+    per warp, block size and grid) against one launch per step and op kind, each captured in a
     CUDA graph together with the reset of the chain states; median of 5 replays."""
     from paper_1502_05216_gb300 import chains, inputs as I
     batch = I.chains(65536)
     cb = chains.ChainBatch(batch, dev)
     cfg, table = cb.tune()
-    fused = cb.time_graph(cb.graph("fused", cfg["threads"], cfg["blocks"]), 5)
+    fused = cb.time_graph(cb.graph("fused", cfg["threads"], cfg["blocks"], cfg["group"]), 5)
     per_op = cb.time_graph(cb.graph("per_op"), 5)
     ops = cb.total_ops
     return {"workload": CHAIN_WORKLOAD, "ops": ops, "mix": dict(zip(("tadd", "tmul", "texp", "tlog"),
@@ -266,7 +266,8 @@ def chains_bench(dev):
             "max_len": cb.max_len, "fused_ms": fused, "per_op_ms": per_op, "speedup": per_op / fused,
             "fused_gops_s": ops / (fused * 1e-3) / 1e9, "fused_config": cfg,
             "per_op_launches": cb.per_op_launches,
-            "tuning": [[r["threads"], r["blocks"], round(r["ms"], 3)] for r in table]}
+            "tuning_cols": ["group", "threads", "blocks", "ms"],
+            "tuning": [[r["group"], r["threads"], r["blocks"], round(r["ms"], 3)] for r in table]}
 
 
 def _time_launches(fn, reps=5, warm=3):

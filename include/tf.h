@@ -173,21 +173,30 @@ enum { TF_OP_ADD = 0, TF_OP_MUL = 1, TF_OP_EXP = 2, TF_OP_LOG = 3 };
 /* Bytes of device workspace tf_chain needs (the work-queue counter). */
 #define TF_CHAIN_WORKSPACE 256
 
-/* All chains in one persistent launch: each warp takes the next 32 chains
- * from an atomic work queue (a counter in `workspace`, reset by this call with
- * an asynchronous memset on `stream`) and runs them to the end, so short and
- * long chains balance across the GPU; no thread ever waits on another.
+/* All chains in one persistent launch: each warp takes the next task (a run
+ * of consecutive chains) from an atomic work queue (a counter in `workspace`,
+ * reset by this call with an asynchronous memset on `stream`) and runs its
+ * chains to the end, so short and long chains balance across the GPU; no
+ * thread ever waits on another.
+ * group: chains per task.  1 .. 32 puts that many chains in every task (one
+ * per lane; lanes beyond it idle).  0 picks it by length: the lanes of a warp
+ * that run different operations at a step pay for all of them, so the longest
+ * chains (above max_len / 1.78) run one per warp, then 2, 4, 8, 16 per warp
+ * down to max_len / 4.7, and the rest 32 per warp; the tiers are found by a
+ * binary search of len, which must then be non-increasing (the step-major
+ * layout above already requires it).  Results do not depend on group,
+ * threads or blocks: every chain runs the same operations in the same order.
  * threads: block size, a multiple of 32 in [32, 1024] that the kernel's register
  * use allows (TF_ERR_ARG otherwise; 512 always fits); blocks: grid size, <= 0
  * for one wave of resident blocks (capped at what n_chains can use).
  * workspace: TF_CHAIN_WORKSPACE bytes of device memory, 8-byte aligned,
  * owned by the caller and used by no other call in flight (concurrent calls
  * need separate workspaces).  len must be 4-byte aligned, the double and
- * int64 arrays 8-byte aligned.  Returns TF_ERR_ARG for a bad block size,
- * TF_ERR_NULL / TF_ERR_SIZE / TF_ERR_ALIGN as the other calls. */
+ * int64 arrays 8-byte aligned.  Returns TF_ERR_ARG for a bad block size or
+ * group, TF_ERR_NULL / TF_ERR_SIZE / TF_ERR_ALIGN as the other calls. */
 int tf_chain(const uint8_t* ops, const double* a0, const double* a1, const int64_t* step_base,
              const int32_t* len, double* s0, double* s1, int64_t n_chains, int32_t max_len,
-             void* workspace, int threads, int blocks, void* stream);
+             void* workspace, int threads, int blocks, int group, void* stream);
 
 /* tf_chain without the caller's workspace, for callers that cannot allocate
  * device memory themselves: code that runs where a host framework owns all of
@@ -211,7 +220,7 @@ int tf_chain(const uint8_t* ops, const double* a0, const double* a1, const int64
 #define TF_CHAIN_NOALLOC_MAX_CHAINS (1LL << 40)
 int tf_chain_noalloc(const uint8_t* ops, const double* a0, const double* a1, const int64_t* step_base,
                      const int32_t* len, double* s0, double* s1, int64_t n_chains, int32_t max_len,
-                     int threads, int blocks, void* stream);
+                     int threads, int blocks, int group, void* stream);
 
 /* One operation kind at one step, for the chains listed in idx[0 .. n_idx)
  * (the per-op baseline: one launch per step and operation kind): for each

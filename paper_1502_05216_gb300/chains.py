@@ -21,9 +21,11 @@ import numpy as np
 
 from . import tf
 
-# block sizes and grids (blocks per SM, 0 = one full wave) the tuner tries
+# block sizes, grids (blocks per SM, 0 = one full wave) and chains per warp
+# (0 = by length, see tf_chain) the tuner tries
 TUNE_THREADS = (32, 64, 128, 256, 512)
 TUNE_BLOCKS_PER_SM = (0, 1, 2)
+TUNE_GROUPS = (0, 8, 32)
 
 
 def per_op_lists(ops: np.ndarray, step_base: np.ndarray, max_len: int):
@@ -78,9 +80,9 @@ class ChainBatch:
             self.s0.copy_(self.init0)
             self.s1.copy_(self.init1)
 
-    def run_fused(self, threads: int = 128, blocks: int = 0, stream=None):
+    def run_fused(self, threads: int = 128, blocks: int = 0, group: int = 0, stream=None):
         tf.chain(self.ops, self.a0, self.a1, self.step_base, self.length, self.s0, self.s1,
-                 self.max_len, self.workspace, threads=threads, blocks=blocks, stream=stream)
+                 self.max_len, self.workspace, threads=threads, blocks=blocks, group=group, stream=stream)
 
     def _build_per_op(self):
         import torch
@@ -102,7 +104,7 @@ class ChainBatch:
                           stream=stream)
 
     # -- CUDA graphs ------------------------------------------------------------------
-    def graph(self, mode: str = "fused", threads: int = 128, blocks: int = 0):
+    def graph(self, mode: str = "fused", threads: int = 128, blocks: int = 0, group: int = 0):
         """A CUDA graph of one whole batch: reset the states, then run it
         (mode "fused" or "per_op").  Replay with .replay()."""
         import torch
@@ -114,17 +116,17 @@ class ChainBatch:
         with torch.cuda.stream(s):
             # one eager run first, so that nothing is first touched under capture
             self.reset(s)
-            self._run(mode, threads, blocks, s)
+            self._run(mode, threads, blocks, group, s)
             s.synchronize()
             with torch.cuda.graph(g, stream=s):
                 self.reset(s)
-                self._run(mode, threads, blocks, s)
+                self._run(mode, threads, blocks, group, s)
         torch.cuda.current_stream(self.device).wait_stream(s)
         return g
 
-    def _run(self, mode, threads, blocks, stream):
+    def _run(self, mode, threads, blocks, group, stream):
         if mode == "fused":
-            self.run_fused(threads, blocks, stream)
+            self.run_fused(threads, blocks, group, stream)
         elif mode == "per_op":
             self.run_per_op(stream)
         else:
@@ -148,18 +150,19 @@ class ChainBatch:
 
     # -- autotuner --------------------------------------------------------------------
     def tune(self, reps: int = 3):
-        """Time every (threads, blocks) candidate of the fused launch on this
-        batch and return (best config dict, table of all timings)."""
+        """Time every (group, threads, blocks) candidate of the fused launch on
+        this batch and return (best config dict, table of all timings)."""
         table = []
-        for th in TUNE_THREADS:
-            for bps in TUNE_BLOCKS_PER_SM:
-                blocks = bps * self.sms
-                g = self.graph("fused", th, blocks)
-                ms = self.time_graph(g, reps)
-                table.append({"threads": th, "blocks": blocks, "ms": ms})
-                del g
+        for grp in TUNE_GROUPS:
+            for th in TUNE_THREADS:
+                for bps in TUNE_BLOCKS_PER_SM:
+                    blocks = bps * self.sms
+                    g = self.graph("fused", th, blocks, grp)
+                    ms = self.time_graph(g, reps)
+                    table.append({"group": grp, "threads": th, "blocks": blocks, "ms": ms})
+                    del g
         best = min(table, key=lambda r: r["ms"])
-        return {"threads": best["threads"], "blocks": best["blocks"]}, table
+        return {"group": best["group"], "threads": best["threads"], "blocks": best["blocks"]}, table
 
     def state(self):
         """Final chain states as numpy arrays (s0, s1)."""

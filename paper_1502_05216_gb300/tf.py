@@ -59,9 +59,9 @@ def load(path: str | None = None):
             f = getattr(lib, "tf_" + name)
             f.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
             f.restype = i32
-        lib.tf_chain.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, ctypes.c_int32, vp, i32, i32, vp]
+        lib.tf_chain.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, ctypes.c_int32, vp, i32, i32, i32, vp]
         lib.tf_chain.restype = i32
-        lib.tf_chain_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, ctypes.c_int32, i32, i32, vp]
+        lib.tf_chain_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, ctypes.c_int32, i32, i32, i32, vp]
         lib.tf_chain_noalloc.restype = i32
         lib.tf_chain_step.argtypes = [i32, vp, i64, i64, vp, vp, vp, vp, vp]
         lib.tf_chain_step.restype = i32
@@ -254,11 +254,12 @@ def _dptr(t, name, dtype, device):
     return t.data_ptr()
 
 
-def chain(ops, a0, a1, step_base, length, s0, s1, max_len, workspace, threads=128, blocks=0, stream=None):
+def chain(ops, a0, a1, step_base, length, s0, s1, max_len, workspace, threads=128, blocks=0, group=0,
+          stream=None):
     """tf_chain: run every chain of a step-major batch to its end in one
     persistent launch; s0/s1 (float64) are updated in place.  ops uint8,
     step_base int64, length int32, workspace a uint8 tensor of
-    CHAIN_WORKSPACE bytes."""
+    CHAIN_WORKSPACE bytes; group = chains per warp (1 .. 32), 0 = by length."""
     import torch
     dev = s0.device
     n = s0.numel()
@@ -272,11 +273,12 @@ def chain(ops, a0, a1, step_base, length, s0, s1, max_len, workspace, threads=12
             _dptr(s1, "s1", torch.float64, dev))
     if not workspace.is_cuda or workspace.device != dev:
         raise TypeError(f"workspace must be on {dev}")
-    _check(load().tf_chain(*args, n, int(max_len), workspace.data_ptr(), int(threads), int(blocks),
+    _check(load().tf_chain(*args, n, int(max_len), workspace.data_ptr(), int(threads), int(blocks), int(group),
                            _stream(stream, dev)), "chain")
 
 
-def chain_noalloc(ops, a0, a1, step_base, length, s0, s1, max_len, threads=128, blocks=0, stream=None):
+def chain_noalloc(ops, a0, a1, step_base, length, s0, s1, max_len, threads=128, blocks=0, group=0,
+                  stream=None):
     """tf_chain_noalloc: as chain() but with the library's static scratch in
     place of a workspace, for callers that cannot allocate device memory (see
     include/tf.h); calls must not overlap on the GPU."""
@@ -289,8 +291,8 @@ def chain_noalloc(ops, a0, a1, step_base, length, s0, s1, max_len, threads=128, 
             _dptr(a1, "a1", torch.float64, dev), _dptr(step_base, "step_base", torch.int64, dev),
             _dptr(length, "length", torch.int32, dev), _dptr(s0, "s0", torch.float64, dev),
             _dptr(s1, "s1", torch.float64, dev))
-    _check(load().tf_chain_noalloc(*args, n, int(max_len), int(threads), int(blocks), _stream(stream, dev)),
-           "chain_noalloc")
+    _check(load().tf_chain_noalloc(*args, n, int(max_len), int(threads), int(blocks), int(group),
+                                   _stream(stream, dev)), "chain_noalloc")
 
 
 def chain_step(op, idx, step_base_t, a0, a1, s0, s1, stream=None):

@@ -66,29 +66,68 @@ def test_fused_equals_per_op_and_oracle(mods):
     print(check_oracle(batch, *f, "4096 chains"))
 
 
-@pytest.mark.parametrize("threads,blocks", [(32, 0), (64, 1), (256, 0), (512, 3), (128, 1000)])
-def test_launch_configs_agree(mods, threads, blocks):
-    """Block size, grid size and the work queue change who runs a chain, never its result."""
+@pytest.mark.parametrize("threads,blocks,group", [(32, 0, 0), (64, 1, 0), (256, 0, 0), (512, 3, 0), (128, 1000, 0),
+                                                (128, 0, 1), (64, 0, 7), (128, 5, 16), (256, 0, 31), (32, 2, 32)])
+def test_launch_configs_agree(mods, threads, blocks, group):
+    """Block size, grid size, chains per warp and the work queue change who runs
+    a chain, never its result."""
     tf, chains = mods
     batch = I.chains(3000, seed=22, mean_len=32.0, cap=300)
     cb = chains.ChainBatch(batch)
     cb.reset()
-    cb.run_fused(128, 0)
+    cb.run_per_op()
     ref = cb.state()
     cb.reset()
-    cb.run_fused(threads, blocks)
+    cb.run_fused(threads, blocks, group)
     got = cb.state()
     assert np.array_equal(ref[0].view(np.int64), got[0].view(np.int64))
     assert np.array_equal(ref[1].view(np.int64), got[1].view(np.int64))
 
 
 def test_too_large_block_is_rejected(mods):
-    """A block size whose registers do not fit is refused before launching."""
+    """A block size whose registers do not fit, or a group outside 0 .. 32, is
+    refused before launching."""
     tf, chains = mods
     batch = I.chains(64, seed=26, mean_len=4.0, cap=8)
     cb = chains.ChainBatch(batch)
     with pytest.raises(tf.TwofoldError, match="invalid argument"):
         cb.run_fused(1024, 0)
+    for g in (-1, 33):
+        with pytest.raises(tf.TwofoldError, match="invalid argument"):
+            cb.run_fused(128, 0, g)
+
+
+def test_length_tiers_cover_every_chain(mods):
+    """The length tiers of group 0 split the chains at max_len / 1.78 .. / 4.7:
+    a batch with lengths at, just above and just below every boundary (and
+    ties across them) runs every chain exactly once, bitwise as the
+    per-operation baseline."""
+    tf, chains = mods
+    rng = np.random.default_rng(27)
+    max_len = 600
+    cuts = [int(max_len / f) for f in (1.78, 2.87, 3.97, 4.58, 4.7)]
+    lens = [max_len] + [c + d for c in cuts for d in (-1, 0, 1) for _ in range(rng.integers(1, 40))]
+    lens += list(rng.integers(1, 120, 3000))
+    base = I.chains(len(lens), seed=28, mean_len=1e9, cap=max_len)   # every chain max_len long
+    L = np.sort(np.array(lens, np.int64))[::-1]
+    # keep each chain's first L steps of the step-major stream (the ops stay feasible)
+    active = np.searchsorted(-L, -np.arange(max_len), side="left")
+    sb = np.zeros(max_len + 1, np.int64)
+    sb[1:] = np.cumsum(active)
+    keep = np.concatenate([np.arange(base["step_base"][t], base["step_base"][t] + active[t]) for t in range(max_len)])
+    batch = {"ops": base["ops"][keep], "a0": base["a0"][keep], "a1": base["a1"][keep], "step_base": sb,
+             "length": L.astype(np.int32), "s0": base["s0"], "s1": base["s1"], "max_len": max_len}
+    cb = chains.ChainBatch(batch)
+    cb.reset()
+    cb.run_per_op()
+    ref = cb.state()
+    for group in (0, 3):
+        cb.reset()
+        cb.run_fused(64, 0, group)
+        got = cb.state()
+        assert np.array_equal(ref[0].view(np.int64), got[0].view(np.int64)), group
+        assert np.array_equal(ref[1].view(np.int64), got[1].view(np.int64)), group
+    check_oracle(batch, *got, "tier boundaries")
 
 
 def test_graphs_replay(mods):
@@ -99,8 +138,8 @@ def test_graphs_replay(mods):
     cb.reset()
     cb.run_fused()
     ref = cb.state()
-    for mode in ("fused", "per_op"):
-        g = cb.graph(mode)
+    for mode, group in (("fused", 0), ("fused", 32), ("per_op", 0)):
+        g = cb.graph(mode, group=group)
         for _ in range(2):
             cb.s0.zero_()
             g.replay()

@@ -49,10 +49,10 @@ def _run(lib, d, batch, noalloc):
     p = [ctypes.c_void_p(x.data_ptr()) for x in (d["ops"], d["a0"], d["a1"], d["sb"], d["len"], s0, s1)]
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     if noalloc:
-        rc = lib.tf_chain_noalloc(*p, n, max_len, 128, 0, stream)
+        rc = lib.tf_chain_noalloc(*p, n, max_len, 128, 0, 0, stream)
     else:
         ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
-        rc = lib.tf_chain(*p, n, max_len, ctypes.c_void_p(ws.data_ptr()), 128, 0, stream)
+        rc = lib.tf_chain(*p, n, max_len, ctypes.c_void_p(ws.data_ptr()), 128, 0, 0, stream)
     assert rc == 0, lib.tf_strerror(rc).decode()
     torch.cuda.synchronize()
     return s0.cpu().numpy(), s1.cpu().numpy()
@@ -74,7 +74,8 @@ def test_noalloc_equals_workspace_entry_point_twice(lib):
 def test_noalloc_rejects_bad_arguments(lib):
     good = ctypes.c_void_p(1 << 20)
     g7 = [good] * 7
-    assert lib.tf_chain_noalloc(*g7, (1 << 40) + 1, 5, 128, 0, None) == 2  # beyond the maximum: TF_ERR_SIZE
-    assert lib.tf_chain_noalloc(*g7, -1, 5, 128, 0, None) == 2
-    assert lib.tf_chain_noalloc(*g7, 10, 5, 48, 0, None) == 6             # TF_ERR_ARG
-    assert lib.tf_chain_noalloc(*g7, 0, 5, 128, 0, None) == 0             # nothing to do
+    assert lib.tf_chain_noalloc(*g7, (1 << 40) + 1, 5, 128, 0, 0, None) == 2  # beyond the maximum: TF_ERR_SIZE
+    assert lib.tf_chain_noalloc(*g7, -1, 5, 128, 0, 0, None) == 2
+    assert lib.tf_chain_noalloc(*g7, 10, 5, 48, 0, 0, None) == 6             # TF_ERR_ARG: block size
+    assert lib.tf_chain_noalloc(*g7, 10, 5, 128, 0, 33, None) == 6           # TF_ERR_ARG: group
+    assert lib.tf_chain_noalloc(*g7, 0, 5, 128, 0, 0, None) == 0             # nothing to do
