@@ -35,18 +35,47 @@ __device__ __forceinline__ void apply_op(int op, double a0, double a1, double& s
     s1 = z1;
 }
 
-// Chains per warp.  The lanes of a warp run different operations, so each
-// step of a warp costs the union of the operations its lanes need: with the
-// batched mix (tadd, tmul 30 % each, texp 17.5 %, tlog 22.4 %) about 1.8, 2.9,
-// 4.0, 4.6 and 4.7 times one chain's step for 2, 4, 8, 16 and 32 chains.  The
+// A cheap operation on a chain's state: tadd, tmul, or an unknown op code,
+// which leaves it unchanged.
+__device__ __forceinline__ void apply_cheap(int op, double a0, double a1, double& s0, double& s1) {
+    double z0 = s0, z1 = s1;
+    if (op == TF_OP_ADD) tf::tadd1(s0, s1, a0, a1, z0, z1);
+    else if (op == TF_OP_MUL) tf::tmul1(s0, s1, a0, a1, z0, z1);
+    s0 = z0;
+    s1 = z1;
+}
+
+// Scheduling inside a warp.  The lanes of a warp run different chains, so a
+// warp that ran every lane's next operation at once would pay, at each step,
+// for every operation kind its lanes need (with the batched mix, texp and tlog
+// both in most steps of a full warp).  A warp of several chains instead
+// alternates two phases:
+//  * cheap: every lane whose next operation is tadd, tmul (or an unknown code)
+//    runs it, again until no lane has a cheap one next;
+//  * costly: of texp and tlog, the warp runs the one whose waiting lanes hold
+//    more remaining steps per unit cost (kCostExp : kCostLog, the ratio of
+//    their instruction counts), for the lanes waiting on it; the other kind
+//    waits a phase.
+// Every lane still runs its own chain's operations in order, so the results
+// are those of any other schedule; the choice only balances the lanes (the
+// lanes with the most work left decide).  A warp of one chain runs its steps
+// one after the other, without the phases' votes.
+constexpr int kCostExp = 7, kCostLog = 10;
+constexpr int kMaxWeight = 1 << 22;  // 32 lanes x 2^22 x 10 < 2^31
+
+// Chains per warp.  A warp's lanes share its phases, so the longest lane of a
+// warp of k chains takes about f(k) times as long as its chain alone would;
+// measured on GB300 with k chains of equal length per warp, one warp per SM
+// sub-partition: f(2, 4, 8, 16, 32) = 1.47, 1.89, 2.42, 3.33, 4.03.  The
 // batch lasts as long as its slowest warp, so the longest chains get the
 // fewest lanes.  Tier j gives kTierK[j] chains to a warp and takes the chains
-// whose length exceeds max_len / kTierF[j + 1] but not max_len / kTierF[j]
-// (kTierF[0] = 1): a chain of length L then finishes within about
-// max_len one-chain steps.  group = k > 0 puts k chains in every warp instead.
+// with max_len / kTierF[j] < L <= max_len / kTierF[j - 1] (kTierF[-1] = 1),
+// kTierF[j] = f(kTierK[j + 1]): a chain of length L then finishes within
+// about max_len one-chain steps.  group = k > 0 puts k chains in every warp
+// instead.
 constexpr int kTiers = 6;
 __constant__ int kTierK[kTiers] = {1, 2, 4, 8, 16, 32};
-__constant__ float kTierF[kTiers] = {1.78f, 2.87f, 3.97f, 4.58f, 4.7f, 1e30f};
+__constant__ float kTierF[kTiers] = {1.47f, 1.89f, 2.42f, 3.33f, 4.03f, 1e30f};
 
 // Number of chains longer than thr (len is non-increasing): a binary search.
 __device__ __forceinline__ int64_t count_longer(const int32_t* __restrict__ len, int64_t n, int64_t thr) {
@@ -59,6 +88,45 @@ __device__ __forceinline__ int64_t count_longer(const int32_t* __restrict__ len,
     return lo;
 }
 
+// A lane's position in its chain: the state, step t's op code and operand,
+// and step t + 1's, loaded one operation ahead so that a chain's sequential
+// steps do not wait on memory.
+struct Cursor {
+    int64_t c;
+    int L, t;
+    int op, opn;
+    double b0, b1, b0n, b1n;
+    int64_t sb2;  // step_base[t + 2]
+    double x0, x1;
+};
+
+// Load step t + 2's op code and operand while step t runs, then advance.
+__device__ __forceinline__ void load_next(Cursor& u, const uint8_t* __restrict__ ops, const double* __restrict__ a0,
+                                          const double* __restrict__ a1, const int64_t* __restrict__ step_base,
+                                          int& op2, double& b02, double& b12, int64_t& sb3) {
+    op2 = 0;
+    b02 = b12 = 0.0;
+    sb3 = 0;
+    if (u.t + 2 < u.L) {
+        int64_t k2 = u.sb2 + u.c;
+        op2 = __ldg(ops + k2);
+        b02 = __ldg(a0 + k2);
+        b12 = __ldg(a1 + k2);
+        sb3 = (u.t + 3 < u.L) ? __ldg(step_base + u.t + 3) : 0;
+    }
+}
+
+__device__ __forceinline__ void advance(Cursor& u, int op2, double b02, double b12, int64_t sb3) {
+    u.op = u.opn;
+    u.b0 = u.b0n;
+    u.b1 = u.b1n;
+    u.opn = op2;
+    u.b0n = b02;
+    u.b1n = b12;
+    u.sb2 = sb3;
+    ++u.t;
+}
+
 // Persistent fused kernel.  Lane 0 of each warp takes the next task from the
 // work queue (one atomicAdd, no waiting): a run of up to k consecutive chains
 // of one tier, which the warp runs to the end before taking more, until the
@@ -69,6 +137,7 @@ __global__ void chain_fused(const uint8_t* __restrict__ ops, const double* __res
                             const double* __restrict__ a1, const int64_t* __restrict__ step_base,
                             const int32_t* __restrict__ len, double* s0, double* s1, int64_t n_chains,
                             int32_t max_len, int group, unsigned long long* queue) {
+    constexpr unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     // tier ends e[j] (chain index) and task counts: lane j < kTiers finds tier j's end
     int64_t e_mine = n_chains;
@@ -80,7 +149,7 @@ __global__ void chain_fused(const uint8_t* __restrict__ ops, const double* __res
     int64_t b = 0;
 #pragma unroll
     for (int j = 0; j < kTiers; ++j) {
-        int64_t ej = __shfl_sync(0xffffffffu, e_mine, j);
+        int64_t ej = __shfl_sync(kAll, e_mine, j);
         ej = (group > 0) ? ((j == kTiers - 1) ? n_chains : 0) : max(ej, b);
         kk[j] = (group > 0) ? group : kTierK[j];
         e[j] = ej;
@@ -90,7 +159,7 @@ __global__ void chain_fused(const uint8_t* __restrict__ ops, const double* __res
     while (true) {
         unsigned long long task = 0;
         if (lane == 0) task = atomicAdd(queue, 1ull);
-        task = __shfl_sync(0xffffffffu, task, 0);
+        task = __shfl_sync(kAll, task, 0);
         if (task >= (unsigned long long)first[kTiers]) break;
         int64_t start = 0, end = 0;
         int k = 32;
@@ -103,43 +172,74 @@ __global__ void chain_fused(const uint8_t* __restrict__ ops, const double* __res
                 end = e[j];
             }
         }
-        int64_t c = start + lane;
-        bool in = (lane < k) && (c < end);
-        int L = in ? len[c] : 0;
-        double x0 = in ? s0[c] : 0.0, x1 = in ? s1[c] : 0.0;
-        // software pipeline: the op code and operand of step t + 1 (and the block
-        // base of step t + 2) are loaded before step t computes, so that a chain's
-        // sequential steps do not wait on memory
-        int op = 0;
-        double b0 = 0.0, b1 = 0.0;
-        int64_t sb1 = 0;
-        if (L > 0) {
-            int64_t k0 = __ldg(step_base) + c;
-            op = __ldg(ops + k0);
-            b0 = __ldg(a0 + k0);
-            b1 = __ldg(a1 + k0);
-            sb1 = (L > 1) ? __ldg(step_base + 1) : 0;
-        }
-        for (int t = 0; t < L; ++t) {
-            int opn = 0;
-            double b0n = 0.0, b1n = 0.0;
-            int64_t sb2 = 0;
-            if (t + 1 < L) {
-                int64_t k1 = sb1 + c;
-                opn = __ldg(ops + k1);
-                b0n = __ldg(a0 + k1);
-                b1n = __ldg(a1 + k1);
-                sb2 = (t + 2 < L) ? __ldg(step_base + t + 2) : 0;
+        Cursor u;
+        u.c = start + lane;
+        bool in = (lane < k) && (u.c < end);
+        u.L = in ? len[u.c] : 0;
+        u.t = 0;
+        u.x0 = in ? s0[u.c] : 0.0;
+        u.x1 = in ? s1[u.c] : 0.0;
+        u.op = u.opn = 0;
+        u.b0 = u.b1 = u.b0n = u.b1n = 0.0;
+        u.sb2 = 0;
+        if (u.L > 0) {
+            int64_t k0 = __ldg(step_base) + u.c;
+            u.op = __ldg(ops + k0);
+            u.b0 = __ldg(a0 + k0);
+            u.b1 = __ldg(a1 + k0);
+            if (u.L > 1) {
+                int64_t k1 = __ldg(step_base + 1) + u.c;
+                u.opn = __ldg(ops + k1);
+                u.b0n = __ldg(a0 + k1);
+                u.b1n = __ldg(a1 + k1);
+                u.sb2 = (u.L > 2) ? __ldg(step_base + 2) : 0;
             }
-            apply_op(op, b0, b1, x0, x1);
-            op = opn;
-            b0 = b0n;
-            b1 = b1n;
-            sb1 = sb2;
+        }
+        if (k == 1) {
+            while (u.t < u.L) {
+                int op2;
+                double b02, b12;
+                int64_t sb3;
+                load_next(u, ops, a0, a1, step_base, op2, b02, b12, sb3);
+                apply_op(u.op, u.b0, u.b1, u.x0, u.x1);
+                advance(u, op2, b02, b12, sb3);
+            }
+        }
+        while (k > 1 && __any_sync(kAll, u.t < u.L)) {
+            // cheap phase
+            while (true) {
+                bool ch = (u.t < u.L) && u.op != TF_OP_EXP && u.op != TF_OP_LOG;
+                if (!__any_sync(kAll, ch)) break;
+                if (ch) {
+                    int op2;
+                    double b02, b12;
+                    int64_t sb3;
+                    load_next(u, ops, a0, a1, step_base, op2, b02, b12, sb3);
+                    apply_cheap(u.op, u.b0, u.b1, u.x0, u.x1);
+                    advance(u, op2, b02, b12, sb3);
+                }
+            }
+            // costly phase: every running lane now waits on texp or tlog
+            const bool run = u.t < u.L;
+            const int w = run ? min(u.L - u.t, kMaxWeight) : 0;
+            const int vote = __reduce_add_sync(kAll, u.op == TF_OP_EXP ? w * kCostLog : -w * kCostExp);
+            const int X = vote >= 0 ? TF_OP_EXP : TF_OP_LOG;
+            if (run && u.op == X) {
+                int op2;
+                double b02, b12;
+                int64_t sb3;
+                load_next(u, ops, a0, a1, step_base, op2, b02, b12, sb3);
+                double z0 = u.x0, z1 = u.x1;
+                if (X == TF_OP_EXP) tf::texp_impl<false, true>(u.x0, u.x1, z0, z1);
+                else tf::tlog_impl<false>(u.x0, u.x1, z0, z1);
+                u.x0 = z0;
+                u.x1 = z1;
+                advance(u, op2, b02, b12, sb3);
+            }
         }
         if (in) {
-            s0[c] = x0;
-            s1[c] = x1;
+            s0[u.c] = u.x0;
+            s1[u.c] = u.x1;
         }
     }
 }
