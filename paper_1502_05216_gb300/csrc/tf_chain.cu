@@ -64,15 +64,17 @@ constexpr int kCostExp = 7, kCostLog = 10;
 constexpr int kMaxWeight = 1 << 22;  // 32 lanes x 2^22 x 10 < 2^31
 
 // Chains per warp.  A warp's lanes share its phases, so the longest lane of a
-// warp of k chains takes about f(k) times as long as its chain alone would;
-// measured on GB300 with k chains of equal length per warp, one warp per SM
-// sub-partition: f(2, 4, 8, 16, 32) = 1.47, 1.89, 2.42, 3.33, 4.03.  The
+// warp of k chains takes about f(k) times as long as its chain alone would.
+// Measured on GB300 with k chains of 800 steps per warp, one warp per SM
+// sub-partition: f(2, 4, 8, 16, 32) = 1.38, 1.78, 2.27, 3.12, 3.77.  The
 // batch lasts as long as its slowest warp, so the longest chains get the
 // fewest lanes.  Tier j gives kTierK[j] chains to a warp and takes the chains
 // with max_len / kTierF[j] < L <= max_len / kTierF[j - 1] (kTierF[-1] = 1),
-// kTierF[j] = f(kTierK[j + 1]): a chain of length L then finishes within
-// about max_len one-chain steps.  group = k > 0 puts k chains in every warp
-// instead.
+// kTierF[j] ~ f(kTierK[j + 1]): a chain of length L then finishes within
+// about max_len one-chain steps.  The table is f raised by about 7 % (a full
+// GPU slows the shared warps a little more than an idle one); on the 65,536-
+// chain batch it measured as fast as 1.15 times it and faster than 0.85 or
+// 1.3 times it.  group = k > 0 puts k chains in every warp instead.
 constexpr int kTiers = 6;
 __constant__ int kTierK[kTiers] = {1, 2, 4, 8, 16, 32};
 __constant__ float kTierF[kTiers] = {1.47f, 1.89f, 2.42f, 3.33f, 4.03f, 1e30f};
