@@ -179,13 +179,15 @@ enum { TF_OP_ADD = 0, TF_OP_MUL = 1, TF_OP_EXP = 2, TF_OP_LOG = 3 };
  * chains to the end, so short and long chains balance across the GPU; no
  * thread ever waits on another.
  * group: chains per task.  1 .. 32 puts that many chains in every task (one
- * per lane; lanes beyond it idle).  0 picks it by length: the lanes of a warp
- * that run different operations at a step pay for all of them, so the longest
- * chains (above max_len / 1.78) run one per warp, then 2, 4, 8, 16 per warp
- * down to max_len / 4.7, and the rest 32 per warp; the tiers are found by a
- * binary search of len, which must then be non-increasing (the step-major
- * layout above already requires it).  Results do not depend on group,
- * threads or blocks: every chain runs the same operations in the same order.
+ * per lane; lanes beyond it idle).  A warp of several chains alternates a
+ * phase that runs every lane's pending tadd/tmul with one that runs texp or
+ * tlog for the lanes waiting on it, so its chains share its time.  0 picks
+ * the group by length: the longest chains (above max_len / 1.47) run one per
+ * warp, then 2, 4, 8, 16 per warp down to max_len / 4.03, and the rest 32 per
+ * warp; the tiers are found by a binary search of len, which must then be
+ * non-increasing (the step-major layout above already requires it).  Results
+ * do not depend on group, threads or blocks: every chain runs the same
+ * operations in the same order.
  * threads: block size, a multiple of 32 in [32, 1024] that the kernel's register
  * use allows (TF_ERR_ARG otherwise; 512 always fits); blocks: grid size, <= 0
  * for one wave of resident blocks (capped at what n_chains can use).

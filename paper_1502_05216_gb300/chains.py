@@ -24,7 +24,7 @@ from . import tf
 # block sizes, grids (blocks per SM, 0 = one full wave) and chains per warp
 # (0 = by length, see tf_chain) the tuner tries
 TUNE_THREADS = (32, 64, 128, 256, 512)
-TUNE_BLOCKS_PER_SM = (0, 1, 2)
+TUNE_BLOCKS_PER_SM = (0, 1, 2, 3, 4)
 TUNE_GROUPS = (0, 8, 32)
 
 
