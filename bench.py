@@ -250,6 +250,44 @@ CHAIN_WORKLOAD = ("65,536 independent chains, lengths geometric (mean 256, cap 4
                   "{tadd, tmul, texp, tlog} (infeasible draws redrawn), states in [2^-20, 2^20], double twofolds")
 
 
+def host_link(dev, nbytes=1 << 30, reps=3):
+    """The GPU's host link, measured: copy-engine copies between pinned host
+    memory and the device, host to device, device to host, and both at once on
+    two streams (GB/s, median of `reps`).  The end-to-end number moves its
+    bytes over this link; SM-driven loads and stores of pinned memory (the
+    zero-copy path) measured the same rates on GB300."""
+    import torch
+    h1 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h2 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d1 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def rate(h2d, d2h):
+        ts = []
+        for _ in range(reps + 1):
+            torch.cuda.synchronize(dev)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(s1)
+            s2.wait_event(e0)
+            if h2d:
+                with torch.cuda.stream(s1):
+                    d1.copy_(h1, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s2):
+                    h2.copy_(d2, non_blocking=True)
+            e2.record(s2)
+            s1.wait_event(e2)
+            e1.record(s1)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return (h2d + d2h) * nbytes / (statistics.median(ts[1:]) * 1e-3) / 1e9
+
+    out = {"h2d_gbs": rate(1, 0), "d2h_gbs": rate(0, 1), "both_gbs": rate(1, 1)}
+    del h1, h2, d1, d2
+    return out
+
+
 def chains_bench(dev):
     """The batched-chains workload: one fused persistent launch (autotuned chains
     per warp, block size and grid) against one launch per step and op kind, each captured in a
@@ -484,8 +522,12 @@ def ours(a, world, rank, local):
             barrier()
             dt = reduce_max((time.perf_counter() - c0) / ke, world, dev)
             e2e[mode] = {"value": elems / dt / 1e9, "ms_per_step": dt * 1e3}
+        link = host_link(dev)
+        moved = (h2d + d2h) / (e2e["zero-copy"]["ms_per_step"] * 1e-3) / 1e9
+        link.update({"achieved_gbs": moved, "frac": moved / link["both_gbs"],
+                     "note": "achieved = (h2d + d2h bytes per step) / zero-copy time per step; frac of both_gbs"})
         e2e = {"value": e2e["zero-copy"]["value"], "unit": "Gelem/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e2e["zero-copy"]["ms_per_step"],
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e["zero-copy"]["ms_per_step"], "link": link,
                "mode": "zero-copy: the kernels load x0/x1 (y0/y1) from pinned host memory and store z0/z1 "
                        "there, over the host link (tf.call_host default)",
                "pipeline": {"value": e2e["pipeline"]["value"], "ms_per_step": e2e["pipeline"]["ms_per_step"],
