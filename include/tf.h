@@ -184,8 +184,11 @@ enum { TF_OP_ADD = 0, TF_OP_MUL = 1, TF_OP_EXP = 2, TF_OP_LOG = 3 };
  * tlog for the lanes waiting on it, so its chains share its time.  0 picks
  * the group by length: the longest chains (above max_len / 1.47) run one per
  * warp, then 2, 4, 8, 16 per warp down to max_len / 4.03, and the rest 32 per
- * warp; the tiers are found by a binary search of len, which must then be
- * non-increasing (the step-major layout above already requires it).  Results
+ * warp; a tier whose tasks, with the longer tiers', outnumber the launch's
+ * warps packs more chains per warp (up to 32), so that batches with many
+ * chains near max_len are not queued one chain per task.  The tiers are found
+ * by a binary search of len, which must then be non-increasing (the
+ * step-major layout above already requires it).  Results
  * do not depend on group, threads or blocks: every chain runs the same
  * operations in the same order.
  * threads: block size, a multiple of 32 in [32, 1024] that the kernel's register

@@ -145,6 +145,11 @@ __global__ void chain_fused(const uint8_t* __restrict__ ops, const double* __res
     int64_t e_mine = n_chains;
     if (group <= 0 && lane < kTiers - 1)
         e_mine = count_longer(len, n_chains, (int64_t)((float)max_len / kTierF[lane]));
+    // A tier whose tasks, with those of the tiers before it, would not all fit
+    // in the launch's warps at once doubles its chains per warp (up to 32): a
+    // batch with many chains near max_len packs them rather than queueing
+    // single-chain tasks behind each other.
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     int64_t e[kTiers], first[kTiers + 1];
     int kk[kTiers];
     first[0] = 0;
@@ -153,9 +158,11 @@ __global__ void chain_fused(const uint8_t* __restrict__ ops, const double* __res
     for (int j = 0; j < kTiers; ++j) {
         int64_t ej = __shfl_sync(kAll, e_mine, j);
         ej = (group > 0) ? ((j == kTiers - 1) ? n_chains : 0) : max(ej, b);
-        kk[j] = (group > 0) ? group : kTierK[j];
+        int kj = (group > 0) ? group : kTierK[j];
+        while (group <= 0 && kj < 32 && first[j] + (ej - b + kj - 1) / kj > warps) kj *= 2;
+        kk[j] = kj;
         e[j] = ej;
-        first[j + 1] = first[j] + (ej - b + kk[j] - 1) / kk[j];
+        first[j + 1] = first[j] + (ej - b + kj - 1) / kj;
         b = ej;
     }
     while (true) {

@@ -138,6 +138,25 @@ def test_length_tiers_cover_every_chain(mods):
     check_oracle(batch, *got, "tier boundaries")
 
 
+@pytest.mark.parametrize("threads,blocks", [(128, 0), (32, 1), (64, 3)])
+def test_equal_length_batch_packs(mods, threads, blocks):
+    """Many chains of the maximum length (every chain in the longest tier):
+    group 0 packs them by the launch's warp count (from one chain per warp up
+    to 32, down to a single small block) and still runs every chain exactly
+    once, bitwise as the per-operation baseline."""
+    tf, chains = mods
+    batch = I.chains(5000, seed=30, mean_len=1e9, cap=40)
+    cb = chains.ChainBatch(batch)
+    cb.reset()
+    cb.run_per_op()
+    ref = cb.state()
+    cb.reset()
+    cb.run_fused(threads, blocks, 0)
+    got = cb.state()
+    assert np.array_equal(ref[0].view(np.int64), got[0].view(np.int64))
+    assert np.array_equal(ref[1].view(np.int64), got[1].view(np.int64))
+
+
 def test_graphs_replay(mods):
     import torch
     tf, chains = mods
