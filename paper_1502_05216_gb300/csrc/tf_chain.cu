@@ -90,9 +90,9 @@ __device__ __forceinline__ int64_t count_longer(const int32_t* __restrict__ len,
     return lo;
 }
 
-// A lane's position in its chain: the state, step t's op code and operand,
-// and step t + 1's, loaded one operation ahead so that a chain's sequential
-// steps do not wait on memory.
+// A lane's position in its chain: the state, and the op codes and operands of
+// steps t and t + 1 in registers.  Step t + 2's are loaded while step t runs,
+// so that a chain's sequential steps do not wait on memory.
 struct Cursor {
     int64_t c;
     int L, t;
