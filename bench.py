@@ -307,22 +307,27 @@ def host_link(dev, nbytes=1 << 30, reps=3):
     return out
 
 
-def chains_bench(dev):
+def chains_bench(dev, rank=0, world=1):
     """The batched-chains workload: one fused persistent launch (autotuned chains
-    per warp, block size and grid) against one launch per step and op kind, each captured in a
-    CUDA graph together with the reset of the chain states; median of 5 replays."""
+    per warp, block size and grid) against one launch per step and op kind, each
+    captured in a CUDA graph together with the reset of the chain states; median
+    of 5 replays.  With N ranks the 65,536 chains are sharded by chain id
+    (chains.shard, strong scaling: the batch is fixed) and the times are the
+    slowest rank's."""
     from paper_1502_05216_gb300 import chains, inputs as I
-    batch = I.chains(65536)
+    full = I.chains(65536)
+    batch = chains.shard(full, rank, world) if world > 1 else full
     cb = chains.ChainBatch(batch, dev)
     cfg, table = cb.tune()
-    fused = cb.time_graph(cb.graph("fused", cfg["threads"], cfg["blocks"], cfg["group"]), 5)
-    per_op = cb.time_graph(cb.graph("per_op"), 5)
-    ops = cb.total_ops
+    fused = reduce_max(cb.time_graph(cb.graph("fused", cfg["threads"], cfg["blocks"], cfg["group"]), 5), world, dev)
+    per_op = reduce_max(cb.time_graph(cb.graph("per_op"), 5), world, dev)
+    ops = int(full["step_base"][-1])
     return {"workload": CHAIN_WORKLOAD, "ops": ops, "mix": dict(zip(("tadd", "tmul", "texp", "tlog"),
-                                                                    batch["mix"].tolist())),
-            "max_len": cb.max_len, "fused_ms": fused, "per_op_ms": per_op, "speedup": per_op / fused,
+                                                                    full["mix"].tolist())),
+            "max_len": int(full["max_len"]), "fused_ms": fused, "per_op_ms": per_op, "speedup": per_op / fused,
             "fused_gops_s": ops / (fused * 1e-3) / 1e9, "fused_config": cfg,
-            "per_op_launches": cb.per_op_launches,
+            "per_op_launches": cb.per_op_launches, "ranks": world,
+            "scaling": "strong (chains sharded by chain id)" if world > 1 else None,
             "tuning_cols": ["group", "threads", "blocks", "ms"],
             "tuning": [[r["group"], r["threads"], r["blocks"], round(r["ms"], 3)] for r in table]}
 
@@ -552,6 +557,8 @@ def ours(a, world, rank, local):
                "pipeline": {"value": e2e["pipeline"]["value"], "ms_per_step": e2e["pipeline"]["ms_per_step"],
                             "mode": "chunked H2D copy, kernel, D2H copy over 3 streams (tf.HostPipeline)"}}
 
+    # every rank runs its shard of the chains (the times are the slowest rank's)
+    chain = None if a.no_chains else chains_bench(dev, rank, world)
     if rank != 0:
         return
     dom = max(FUNCS, key=lambda f: kern_ms[f])
@@ -587,7 +594,6 @@ def ours(a, world, rank, local):
         per[f] = {"ms": kern_ms[f], "gelem_s": n / t / 1e9, "hbm_gbs": BYTES_PER_ELEM[f] * n / t / 1e9,
                   "alu_frac": fr["alu"], "fp64_frac": fr["fp64"], "hbm_frac": fr["hbm"],
                   "binding": b, "binding_frac": fr[b]}
-    chain = None if a.no_chains else chains_bench(dev)
     sweep = None if (a.no_sweep or a.log2n < 26 or "texp" not in dargs or "tlog" not in dargs) else size_sweep(dev, dargs, a.sweep_max)
     tier = None if a.no_tier else precision_tier(dev, a.tier_log2n)
     coupled = (None if a.no_coupled or not {"texp", "texpm1", "tlog", "tlog1p"} <= set(dargs)

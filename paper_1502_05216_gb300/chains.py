@@ -28,6 +28,29 @@ TUNE_BLOCKS_PER_SM = (0, 1, 2, 3, 4)
 TUNE_GROUPS = (0, 8, 32)
 
 
+def shard(batch: dict, rank: int, world: int) -> dict:
+    """Rank ``rank``'s share of a step-major batch for ``world`` GPUs: the
+    chains c with c % world == rank, as a step-major batch of their own.  The
+    chains keep their longest-first order, so every rank gets an even mix of
+    long and short chains, and each chain keeps its state and its operations
+    in order: a shard's results are those chains' results of the whole
+    batch.  No data moves between ranks (the chains are independent)."""
+    L = np.asarray(batch["length"], dtype=np.int64)
+    ids = np.arange(rank, L.size, world, dtype=np.int64)
+    Ls = L[ids]
+    max_len = int(Ls[0]) if ids.size else 0
+    active = np.searchsorted(-Ls, -np.arange(max_len), side="left")  # shard chains with L > t
+    sb = np.zeros(max_len + 1, dtype=np.int64)
+    sb[1:] = np.cumsum(active)
+    t_of = np.repeat(np.arange(max_len, dtype=np.int64), active)
+    keep = np.asarray(batch["step_base"], dtype=np.int64)[t_of] + ids[np.arange(t_of.size) - sb[t_of]]
+    out = {"ops": batch["ops"][keep], "a0": batch["a0"][keep], "a1": batch["a1"][keep], "step_base": sb,
+           "length": Ls.astype(np.int32), "s0": batch["s0"][ids], "s1": batch["s1"][ids], "max_len": max_len,
+           "ids": ids}
+    out["mix"] = np.bincount(out["ops"], minlength=4)
+    return out
+
+
 def per_op_lists(ops: np.ndarray, step_base: np.ndarray, max_len: int):
     """Index lists of the per-operation baseline: for every step t and op kind,
     the chains (positions within step t's block) that apply that op, all

@@ -4,7 +4,7 @@ the operations of every chain in order."""
 import numpy as np
 
 from paper_1502_05216_gb300 import inputs as I
-from paper_1502_05216_gb300.chains import per_op_lists
+from paper_1502_05216_gb300.chains import per_op_lists, shard
 
 
 def test_generator_layout_and_ranges():
@@ -61,3 +61,34 @@ def test_per_op_lists_replay_each_chain():
         want = [(t, int(b["ops"][b["step_base"][t] + c])) for t in range(int(b["length"][c]))
                 if b["ops"][b["step_base"][t] + c] < 4]
         assert seq[c] == want, c
+
+
+def _chain_ops(b, c):
+    """(ops, a0, a1) of chain c of a step-major batch, in step order."""
+    k = b["step_base"][:b["length"][c]] + c
+    return b["ops"][k], b["a0"][k], b["a1"][k]
+
+
+def test_shards_partition_the_batch():
+    """The shards of 3 ranks are disjoint, cover every chain, are step-major
+    batches themselves (non-increasing lengths, consistent step_base), and
+    hold each chain's state and operations unchanged."""
+    b = I.chains(1001, seed=43, mean_len=30.0, cap=200)
+    world = 3
+    seen = np.zeros(1001, bool)
+    for r in range(world):
+        s = shard(b, r, world)
+        assert not seen[s["ids"]].any()
+        seen[s["ids"]] = True
+        L, sb = s["length"], s["step_base"]
+        assert np.all(np.diff(L) <= 0) and s["max_len"] == L[0]
+        assert np.array_equal(np.diff(sb), [(L > t).sum() for t in range(s["max_len"])])
+        assert sb[-1] == s["ops"].size == L.sum()
+        assert np.array_equal(s["s0"], b["s0"][s["ids"]]) and np.array_equal(s["s1"], b["s1"][s["ids"]])
+        for j in (0, 1, L.size // 2, L.size - 1):
+            for x, y in zip(_chain_ops(s, j), _chain_ops(b, s["ids"][j])):
+                assert np.array_equal(x, y)
+        # the longest-first order gives every rank an even share of the work
+        assert abs(L.sum() / (b["length"].sum() / world) - 1) < 0.1
+    assert seen.all()
+    assert shard(b, 0, 1)["ops"].tobytes() == b["ops"].tobytes()
