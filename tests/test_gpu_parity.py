@@ -210,3 +210,43 @@ def test_hard_cases_2p24(tf, func):
     against the oracle."""
     st = check(tf, func, I.hard_cases(func, 2**24, seed=29), f"{func} hard cases 2^24")
     print(func, st)
+
+
+@pytest.mark.parametrize("func", ("texp", "tmul"))
+@pytest.mark.parametrize("aligned", [True, False])
+def test_beyond_2p31_elements(tf, func, aligned):
+    """n = 2^31 + 5 elements (64-bit element indices, 16 GiB per array): the
+    128-bit vector kernel (aligned) and the scalar one (the input offset by one
+    element).  x0 = -700 + 1400 ((40503 i) mod 2^16) / 2^16 is made on the
+    device from the element index i, with exact operations, so the host
+    reproduces it bit for bit; x1 = NULL (dotted), and tmul squares x0 (both
+    operands the same array).  Outputs at both ends, around 2^30 and 2^31 and
+    at 4096 random indices are checked against the oracle."""
+    import torch
+    n = (1 << 31) + 5
+    off = 0 if aligned else 1
+    buf = torch.empty(n + off, dtype=torch.float64, device="cuda:0")
+    x0 = buf[off:]
+    chunk = 1 << 28
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        i = torch.arange(s, e, dtype=torch.int64, device="cuda:0")
+        x0[s:e] = ((i * 40503) % 65536).to(torch.float64) * (1400.0 / 65536) - 700.0
+        del i
+    z0, z1 = tf.FUNCS[func](x0, None) if func == "texp" else tf.FUNCS[func](x0, None, x0, None)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(31)
+    idx = np.unique(np.concatenate([np.arange(0, 8), np.arange((1 << 30) - 4, (1 << 30) + 4),
+                                    np.arange((1 << 31) - 8, (1 << 31) + 4), np.arange(n - 8, n),
+                                    rng.integers(0, n, 4096)]))
+    ti = torch.from_numpy(idx).to("cuda:0")
+    h0, h1 = z0[ti].cpu().numpy(), z1[ti].cpu().numpy()
+    hx = x0[ti].cpu().numpy()
+    del z0, z1, x0, buf, ti
+    torch.cuda.empty_cache()
+    want = ((idx * 40503) % 65536).astype(np.float64) * (1400.0 / 65536) - 700.0
+    assert np.array_equal(hx.view(np.int64), want.view(np.int64)), "device inputs differ from the host formula"
+    args = (want, None) if func == "texp" else (want, None, want, None)
+    orc = oracle.evaluate(func, *args)
+    st = tfcheck.check(h0, h1, orc, "f64", 0.99999, f"{func} n=2^31+5 aligned={aligned}", func, args)
+    print(func, aligned, st)
