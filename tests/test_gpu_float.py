@@ -135,3 +135,40 @@ def test_precision_tier_same_x0(tf, func):
     std = tfcheck.check(z0.cpu().numpy(), z1.cpu().numpy(), orc, "f64", 0.99999, f"{func} tier", func, (x0d, x1d))
     print(f"tier {func}: f32 max 2^{stf['max_rel_log2']:.1f} mean 2^{stf['mean_rel_log2']:.1f} | "
           f"f64 max 2^{std['max_rel_log2']:.1f} mean 2^{std['mean_rel_log2']:.1f}")
+
+
+@pytest.mark.parametrize("aligned", [True, False])
+def test_beyond_2p31_elements_f32(tf, aligned):
+    """n = 2^31 + 7 float twofolds (64-bit element indices, 8 GiB per array):
+    the 4-wide vector kernel (aligned) and the scalar one (offset by one
+    element).  x0 = -80 + 160 ((40503 i) mod 2^16) / 2^16 is made on the device
+    from the index with exact float operations (the host reproduces it bit for
+    bit), x1 = NULL.  Outputs at both ends, around 2^30 and 2^31 and at 4096
+    random indices are checked against the oracle."""
+    import torch
+    n = (1 << 31) + 7
+    off = 0 if aligned else 1
+    buf = torch.empty(n + off, dtype=torch.float32, device="cuda:0")
+    x0 = buf[off:]
+    chunk = 1 << 28
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        i = torch.arange(s, e, dtype=torch.int64, device="cuda:0")
+        x0[s:e] = ((i * 40503) % 65536).to(torch.float32) * (160.0 / 65536) - 80.0
+        del i
+    z0, z1 = tf.FUNCS_F["texp"](x0, None)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(37)
+    idx = np.unique(np.concatenate([np.arange(0, 8), np.arange((1 << 30) - 4, (1 << 30) + 4),
+                                    np.arange((1 << 31) - 8, (1 << 31) + 4), np.arange(n - 8, n),
+                                    rng.integers(0, n, 4096)]))
+    ti = torch.from_numpy(idx).to("cuda:0")
+    h0, h1, hx = z0[ti].cpu().numpy(), z1[ti].cpu().numpy(), x0[ti].cpu().numpy()
+    del z0, z1, x0, buf, ti
+    torch.cuda.empty_cache()
+    want = (((idx * 40503) % 65536).astype(np.float32) * np.float32(160.0 / 65536) - np.float32(80.0))
+    assert np.array_equal(hx.view(np.int32), want.view(np.int32)), "device inputs differ from the host formula"
+    orc = oracle.evaluate("texp", want.astype(np.float64), None, dtype="f32")
+    st = tfcheck.check(h0.astype(np.float64), h1.astype(np.float64), orc, "f32", 0.99999,
+                       f"texpf n=2^31+7 aligned={aligned}")
+    print(aligned, st)
