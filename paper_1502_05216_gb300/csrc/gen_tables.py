@@ -4,9 +4,9 @@ Run:  python gen_tables.py > tf_tables.h   (the build checks the file is current
 
 All values come from Python's decimal module at 120 significant digits.
 
-  TF_C0     ln2/256 rounded down to 35 significant bits, so that N*C0 is exact
-      for |N| < 2^19 (argument reduction x = N ln2/256 + r).
-  TF_INV_C  256/ln2 rounded to double.
+  TF_C0     ln2/65536 rounded down to 26 significant bits, so that N*C0 is exact
+      for |N| < 2^27 (argument reduction x = N ln2/65536 + r).
+  TF_INV_C  65536/ln2 rounded to double.
 
 Float twofold (float-float on the FP32 pipes) constants:
   TF_F_INV_C   512/ln2 rounded to float.
@@ -22,13 +22,18 @@ Float twofold (float-float on the FP32 pipes) constants:
 
 Fixed-point constants of the integer exp core (unsigned integers, rounded to
 nearest, each with its unit):
-  TF_TFIX[j]   2^(j/256), units 2^-127, as (lo64, hi64), j = -128 .. 128: the
-      table of the reduction x = k ln2 + j ln2/256 + r (a 2^8-step version of
-      the paper's tabulated e^c, "Twofold exponent" > "Function pexp0()");
-      e^c - 1 of "Function pexpm10()" is TF_TFIX[j] - 2^127, exactly.
+  TF_TFIX[j]   2^(j/65536), units 2^-127, as (lo64, hi64), j = -32768 .. 32768:
+      the table of the reduction x = k ln2 + j ln2/65536 + r (a 2^16-step
+      version of the paper's tabulated e^c, "Twofold exponent" > "Function
+      pexp0()"); e^c - 1 of "Function pexpm10()" is TF_TFIX[j] - 2^127,
+      exactly.  1 MiB; computed by exact integer iteration of 2^(1/65536) at
+      256 bits and rounded to nearest.
   TF_HC_m      1/(m+1)!, the coefficients of H(r) = (e^r - 1)/r = sum r^m/(m+1)!:
-      m = 0 .. 4 in units 2^-127 as (lo64, hi64), m = 5 .. 9 in units 2^-72.
-  TF_C12FIX    ln2/256 - C0 (> 0), units 2^-148: the tail of the reduction constant.
+      m = 0 .. 4 in units 2^-127 as (lo64, hi64), m = 5 .. 9 in units 2^-72
+      (the degree-9 H of the logarithm's Newton step).
+  TF_HC68_m    1/(m+1)!, m = 3 .. 6, units 2^-68 (the 64-bit levels of the
+      degree-6 H of the exp core).
+  TF_C12FIX    ln2/65536 - C0 (> 0), units 2^-148: the tail of the reduction constant.
   TF_LN2FIX    ln2, units 2^-128 (the n ln2 term of the logarithm).
   TF_LOGT[i] for i = 724 .. 1448 (z = i/1024 covers [sqrt(1/2), sqrt(2))):
       {-log(c_i) in units 2^-128 as a two's complement (lo64, hi64), C_i, the
@@ -91,18 +96,37 @@ def hexd(x):
     return float.hex(x)
 
 
+def pow2_table(steps, half, unit):
+    """round(2^(j/steps) 2^unit) for j = -half .. half: each power by exact
+    integer multiplication of a 256-bit fixed-point 2^(+-1/steps) (taken from a
+    120-digit decimal value), truncated per step; the accumulated error stays
+    below 2^-230 relative, far inside the final rounding to 2^-unit."""
+    P = 256
+    scale = CTX.power(D(2), P)  # exact at 120 digits (2^256 has 78)
+    up = int(CTX.multiply(CTX.power(D(2), CTX.divide(D(1), steps)), scale))
+    dn = int(CTX.multiply(CTX.power(D(2), CTX.divide(D(-1), steps)), scale))
+    pos, neg = [1 << P], [1 << P]
+    for _ in range(half):
+        pos.append(pos[-1] * up >> P)
+        neg.append(neg[-1] * dn >> P)
+    half_unit = 1 << (P - unit - 1)
+    vals = neg[:0:-1] + pos
+    return [(v + half_unit) >> (P - unit) for v in vals]
+
+
 def main(out=sys.stdout):
     ln2 = CTX.ln(D(2))
-    c = CTX.divide(ln2, 256)
-    C0 = trunc_bits(c, 35)
-    inv_c = float(CTX.divide(256, ln2))
+    c = CTX.divide(ln2, 65536)
+    C0 = trunc_bits(c, 26)
+    inv_c = float(CTX.divide(65536, ln2))
     w = out.write
     w("/* Generated by gen_tables.py -- do not edit.  Constants of the twofold exp/log\n"
       "   kernels, from 120-digit decimal values. */\n")
     w("#pragma once\n\n")
     w("#ifndef TF_TABLE_QUALIFIER\n#define TF_TABLE_QUALIFIER static const\n#endif\n\n")
-    w(f"#define TF_TAB_HALF 128       /* table index j = -128 .. 128, step ln2/256 */\n")
-    w(f"#define TF_INV_C {hexd(inv_c)}  /* 256/ln2 */\n")
+    w(f"#define TF_TAB_BITS 16\n")
+    w(f"#define TF_TAB_HALF 32768     /* table index j = -32768 .. 32768, step ln2/65536 */\n")
+    w(f"#define TF_INV_C {hexd(inv_c)}  /* 65536/ln2 */\n")
     w(f"#define TF_C0 {hexd(C0)}\n")
     w("\n")
     # float twofold constants
@@ -160,8 +184,13 @@ def main(out=sys.stdout):
             x = fixed(v, 72)
             assert x < 2**64
             w(f"#define TF_HC_{m} 0x{x:016x}ull\n")
+    w("/* coefficients 1/(m+1)! of the exp core's H, m = 3 .. 6, units 2^-68 */\n")
+    for m in range(3, 7):
+        x = fixed(CTX.divide(1, D(math.factorial(m + 1))), 68)
+        assert x < 2**64
+        w(f"#define TF_HC68_{m} 0x{x:016x}ull\n")
     c12 = CTX.subtract(c, D(C0))
-    assert c12 > 0
+    assert c12 > 0 and fixed(c12, 148) < 2**106
     w(f"#define TF_C12FIX {{{u128(fixed(c12, 148))}}}\n\n")
     w(f"#define TF_LN2FIX {{{u128(fixed(ln2, 128))}}}\n\n")
     w("/* coefficients (-1)^m/(m+1) of log1p(t)/t, units 2^-62, two's complement */\n")
@@ -211,11 +240,10 @@ def main(out=sys.stdout):
         assert 2**127 <= x < 2**128
         w(f"  {{{u128(x)}, 0x{ee & (2**64 - 1):016x}ull, 0ull}},\n")
     w("};\n\n")
-    w("/* 2^(j/256) in units of 2^-127 as {lo64, hi64}; index j + 128 */\n")
-    w("TF_TABLE_QUALIFIER unsigned long long TF_TFIX_TABLE[257][2] = {\n")
-    for j in range(-128, 129):
-        v = CTX.power(D(2), CTX.divide(D(j), 256))
-        w(f"  {{{u128(fixed(v, 127))}}},\n")
+    w("/* 2^(j/65536) in units of 2^-127 as {lo64, hi64}; index j + 32768 */\n")
+    w("TF_TABLE_QUALIFIER unsigned long long TF_TFIX_TABLE[65537][2] = {\n")
+    for v in pow2_table(65536, 32768, 127):
+        w(f"  {{{u128(v)}}},\n")
     w("};\n\n")
 
 

@@ -5,9 +5,9 @@ The build refuses a header that differs from its generator's output; this test
 checks the generator's output itself, entry by entry (every entry of the small
 tables, a stride of the large ones), from the definitions stated in the kernels:
 
-  TF_TFIX_TABLE[j]  2^(j/256) in units 2^-127 (round to nearest)
-  TF_HC_m           1/(m+1)! in units 2^-127 (m <= 4) or 2^-72
-  TF_LN2FIX         ln 2 in units 2^-128;  TF_C0 + TF_C12FIX 2^-148 = ln2/256
+  TF_TFIX_TABLE[j]  2^(j/65536) in units 2^-127 (round to nearest)
+  TF_HC_m           1/(m+1)! in units 2^-127 (m <= 4) or 2^-72;  TF_HC68_m in units 2^-68
+  TF_LN2FIX         ln 2 in units 2^-128;  TF_C0 + TF_C12FIX 2^-148 = ln2/65536
   TF_LG_m           (-1)^m / (m+1) in units 2^-62
   TF_LOGT[i]        {-log c_i in units 2^-128, C_i = round(2^34 / i), c_i = C_i 2^-24 as a double}
   TF_PX_C[n]        e^(n/256) in units 2^-124
@@ -63,10 +63,10 @@ def _f32(x):
 
 def test_exp_table_and_constants():
     tab = _ints("TF_TFIX_TABLE", 2)
-    assert len(tab) == 257
-    for j in range(-128, 129):
-        lo, hi = tab[j + 128]
-        assert lo | (hi << 64) == _fx(C.power(2, C.divide(D(j), 256)), 127), j
+    assert len(tab) == 65537
+    for j in list(range(-32768, 32769, 97)) + [-32768, -1, 0, 1, 32767, 32768]:
+        lo, hi = tab[j + 32768]
+        assert lo | (hi << 64) == _fx(C.power(2, C.divide(D(j), 65536)), 127), j
     fact = 1
     for m in range(10):
         fact *= m + 1
@@ -74,11 +74,15 @@ def test_exp_table_and_constants():
         d = _define(f"TF_HC_{m}")
         got = _u128(d) if m <= 4 else int(d.rstrip("ul").replace("0x", ""), 16)
         assert got == _fx(v, 127 if m <= 4 else 72), m
+        if 3 <= m <= 6:
+            assert int(_define(f"TF_HC68_{m}").rstrip("ul").replace("0x", ""), 16) == _fx(v, 68), m
     assert _u128(_define("TF_LN2FIX")) == _fx(LN2, 128)
     c0 = D(float.fromhex(_define("TF_C0")))
     c12 = C.multiply(D(_u128(_define("TF_C12FIX"))), C.power(2, -148))
-    assert abs(C.subtract(C.add(c0, c12), C.divide(LN2, 256))) < C.power(2, -148)
-    assert float.fromhex(_define("TF_INV_C")) == float(C.divide(256, LN2))
+    assert abs(C.subtract(C.add(c0, c12), C.divide(LN2, 65536))) < C.power(2, -148)
+    # C0 has at most 26 significant bits (N C0 exact for |N| < 2^27)
+    assert (c0 * D(2) ** 42) == int(c0 * D(2) ** 42) and c0 * D(2) ** 42 < 2**26
+    assert float.fromhex(_define("TF_INV_C")) == float(C.divide(65536, LN2))
     for m in range(5):
         v = int(_define(f"TF_LG_{m}").split("0x")[1].rstrip("ul)"), 16)
         v = v - (1 << 64) if v >> 63 else v
