@@ -45,6 +45,10 @@ nearest, each with its unit):
       TF_PX_C[n] = e^(n/256), n = -511 .. 511, units 2^-124 as (lo64, hi64);
       TF_PX_E[m] = e^(2m) = E_m 2^e_m, m = -373 .. 373, as {lo64, hi64, e_m, 0}
       with E_m in [2^127, 2^128) (rounded to nearest).
+  TF_LOG2T[j] for j = -200 .. 200: {-log(c2_j) in units 2^-128 as a two's
+      complement (lo64, hi64), C2_j, 0} with c2_j = C2_j 2^-24, C2_j =
+      round(2^42 / (2^18 + j)): the second reciprocal table of the logarithm,
+      t2 = (1 + t) c2_j - 1 with j = round(2^18 t), |t2| < 2^-18.9.
   TF_LG_m      (-1)^m / (m+1), m = 0 .. 4, units 2^-62 (two's complement): the
       coefficients of log1p(t)/t.
 """
@@ -213,6 +217,19 @@ def main(out=sys.stdout):
         assert D(cd) == c
         Lu = L & (2**128 - 1)
         w(f"  {{0x{Lu & (2**64 - 1):016x}ull, 0x{Lu >> 64:016x}ull, {C}ull, 0x{struct.unpack('<Q', struct.pack('<d', cd))[0]:016x}ull}},\n")
+    w("};\n\n")
+    w("#define TF_LOG2T_HALF 200\n")
+    w("/* {-log(c2_j) units 2^-128 as (lo64, hi64), C2_j, 0} for j = -200 .. 200,\n"
+      "   c2_j = C2_j 2^-24, C2_j = round(2^42 / (2^18 + j)) */\n")
+    w("TF_TABLE_QUALIFIER unsigned long long TF_LOG2T[401][4] = {\n")
+    for j in range(-200, 201):
+        C = int(CTX.divide(D(2**42), D(2**18 + j)).to_integral_value(rounding=decimal.ROUND_HALF_EVEN))
+        c = CTX.divide(D(C), D(2**24))
+        L = fixed(CTX.minus(CTX.ln(c)), 128)
+        for t1 in (D(j) / 2**18 - D(1) / 2**19, D(j) / 2**18 + D(1) / 2**19):
+            assert abs(CTX.subtract(CTX.multiply(1 + t1, c), 1)) < D(2) ** D("-18.9"), (j, t1)
+        Lu = L & (2**128 - 1)
+        w(f"  {{0x{Lu & (2**64 - 1):016x}ull, 0x{Lu >> 64:016x}ull, {C}ull, 0ull}},\n")
     w("};\n\n")
     # the paper's reduction: K = 8, L = 1
     w("#define TF_PX_CHALF 511\n#define TF_PX_EHALF 373\n")

@@ -8,7 +8,8 @@ tables, a stride of the large ones), from the definitions stated in the kernels:
   TF_TFIX_TABLE[j]  2^(j/65536) in units 2^-127 (round to nearest)
   TF_HC_m           1/(m+1)! in units 2^-127 (m <= 4) or 2^-72;  TF_HC68_m in units 2^-68
   TF_LN2FIX         ln 2 in units 2^-128;  TF_C0 + TF_C12FIX 2^-148 = ln2/65536
-  TF_LG_m           (-1)^m / (m+1) in units 2^-62
+  TF_LG_m           (-1)^m / (m+1) in units 2^-62, m = 0 .. 4
+  TF_LOG2T[j]       {-log c2_j in units 2^-128, C2_j = round(2^42 / (2^18 + j)), 0}
   TF_LOGT[i]        {-log c_i in units 2^-128, C_i = round(2^34 / i), c_i = C_i 2^-24 as a double}
   TF_PX_C[n]        e^(n/256) in units 2^-124
   TF_PX_E[m]        e^(2m) = E 2^e, E in [2^127, 2^128)
@@ -104,6 +105,23 @@ def test_log_table():
         for z in (D(i) / 1024 - D(1) / 2048, D(i) / 1024 + D(1) / 2048):
             z = min(max(z, D("0.7071067811865475")), D("1.414213562373095"))
             assert abs(C.subtract(C.multiply(z, c), 1)) < D(2) ** D("-10.4")
+
+
+def test_second_log_table():
+    tab = _ints("TF_LOG2T", 4)
+    assert len(tab) == 401 and int(_define("TF_LOG2T_HALF")) == 200
+    for j in range(-200, 201):
+        lo, hi, C2, zero = tab[j + 200]
+        assert C2 == int(C.divide(D(2) ** 42, D(2**18 + j)).to_integral_value(rounding=decimal.ROUND_HALF_EVEN))
+        assert zero == 0
+        c = C.multiply(D(C2), C.power(2, -24))
+        L = lo | (hi << 64)
+        L = L - (1 << 128) if L >> 127 else L
+        assert L == _fx(C.minus(C.ln(c)), 128), j
+        # the second reduced argument stays below 2^-18.9 over the cell of t1
+        for t1 in (D(j) / 2**18 - D(1) / 2**19, D(j) / 2**18 + D(1) / 2**19):
+            assert abs(C.subtract(C.multiply(1 + t1, c), 1)) < D(2) ** D("-18.9")
+    assert tab[200][2] == 1 << 24 and tab[200][0] == tab[200][1] == 0  # j = 0: c2 = 1
 
 
 def test_paper_reduction_tables():
