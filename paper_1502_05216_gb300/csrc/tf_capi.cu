@@ -34,7 +34,8 @@ struct OpLog {
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1(a, b, z0, z1); }
 };
 struct OpLog1p {
-    static constexpr int min_blocks = 4;  // 64 registers: 32 warps per SM
+    static constexpr int threads = 128;   // 72 registers: 28 warps per SM
+    static constexpr int min_blocks = 7;
     static constexpr double dummy = 0.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1p1(a, b, z0, z1); }
 };
@@ -66,7 +67,8 @@ struct OpPLog {
 };
 struct OpPLog1p {
     static constexpr double dummy = 0.0;
-    static constexpr int min_blocks = 4;
+    static constexpr int threads = 128;
+    static constexpr int min_blocks = 7;
     __device__ static void eval(double a, double b, double& z0, double& z1) {
         tf::tlog1p1(a, b, z0, z1);
         tf::couple(z0, z1);
@@ -89,7 +91,8 @@ struct OpLogP {
 };
 struct OpLog1pP {
     static constexpr double dummy = 0.0;
-    static constexpr int min_blocks = 4;
+    static constexpr int threads = 128;
+    static constexpr int min_blocks = 7;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1p_impl<false>(a, b, z0, z1); }
 };
 struct OpExpTables {
@@ -130,11 +133,24 @@ __device__ __forceinline__ void st2(double* p, double a, double b) {
     __stcs(reinterpret_cast<double2*>(p), make_double2(a, b));  // streaming: outputs are not re-read
 }
 
+// Block size of an op's vector kernel: Op::threads where the op sets it, else
+// kThreads.  With min_blocks it sets the register budget: 256 x 4 blocks gives
+// 64 registers (32 warps per SM); 128 x 7 gives 72 (28 warps), which the
+// two-table log of tlog1p needs to run without spills.
+template <class Op, class = void>
+struct OpThreads {
+    static constexpr int value = kThreads;
+};
+template <class Op>
+struct OpThreads<Op, decltype((void)Op::threads)> {
+    static constexpr int value = Op::threads;
+};
+
 // Unary, 2 elements per thread, 128-bit I/O.  Thread t covers elements 2t, 2t+1.
 template <class Op>
-__global__ void __launch_bounds__(kThreads, Op::min_blocks) unary_v2(const double* __restrict__ x0, const double* __restrict__ x1,
-                                                     double* z0, double* z1, int64_t n) {
-    int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+__global__ void __launch_bounds__(OpThreads<Op>::value, Op::min_blocks) unary_v2(const double* __restrict__ x0,
+                                                     const double* __restrict__ x1, double* z0, double* z1, int64_t n) {
+    int64_t t = (int64_t)blockIdx.x * OpThreads<Op>::value + threadIdx.x;
     int64_t i = 2 * t;
     double a0 = Op::dummy, a1 = Op::dummy, b0 = 0.0, b1 = 0.0;
     bool full = i + 1 < n;
@@ -288,9 +304,10 @@ int run_unary(const double* x0, const double* x1, double* z0, double* z1, int64_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     bool vec = al(x0, 16) && al(z0, 16) && al(z1, 16) && (!x1 || al(x1, 16));
     if (vec) {
+        constexpr int T = OpThreads<Op>::value;
         int64_t threads = (n + 1) / 2;
-        unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
-        unary_v2<Op><<<blocks, kThreads, 0, s>>>(x0, x1, z0, z1, n);
+        unsigned blocks = (unsigned)((threads + T - 1) / T);
+        unary_v2<Op><<<blocks, T, 0, s>>>(x0, x1, z0, z1, n);
     } else {
         unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
         unary_v1<Op><<<blocks, kThreads, 0, s>>>(x0, x1, z0, z1, n);
