@@ -48,7 +48,7 @@ WORKLOAD = ("texp, texpm1, tlog, tlog1p (+ tadd, tmul) over double twofolds, n=2
 #   x 64 per SM per cycle x active cycles / n (16 lanes per SM sub-partition: the
 #   same derivation with the issue rate reproduces smsp__inst_executed exactly).
 FP64_PER_ELEM = {"texp": 9.0, "texpm1": 10.0, "tlog": 11.0, "tlog1p": 18.0, "tadd": 5.0, "tmul": 4.0}
-ALU_PER_ELEM = {"texp": 295.0, "texpm1": 385.0, "tlog": 496.0, "tlog1p": 598.0, "tadd": 33.0, "tmul": 25.0}
+ALU_PER_ELEM = {"texp": 295.0, "texpm1": 385.0, "tlog": 496.0, "tlog1p": 587.0, "tadd": 33.0, "tmul": 25.0}
 COUNT_SOURCE = "ncu pipe counters, one --set full capture per kernel at n=2^25"
 ALU_LANES_PER_SM_CLK = 64
 # HBM bytes per element: SoA doubles in + out.
@@ -59,14 +59,14 @@ SM_MAX_MHZ = 2070.0     # MEASURED_PEAKS.json sm_max_mhz (used when no clock sam
 # same captures at n = 2^25, scaled by 2 to the benchmark's n = 2^26 (the traffic
 # of an elementwise kernel is proportional to n).  The writes still held in L2 when
 # a launch ends are not in its count.
-TRAFFIC_PER_LAUNCH = {"texp": 2.0510e9, "texpm1": 2.0520e9, "tlog": 2.0470e9, "tlog1p": 2.0507e9,
+TRAFFIC_PER_LAUNCH = {"texp": 2.0510e9, "texpm1": 2.0520e9, "tlog": 2.0470e9, "tlog1p": 2.0472e9,
                       "tadd": 3.1480e9, "tmul": 3.1481e9}
 TRAFFIC_N = 1 << 26
 # Pipe utilisation of the same captures (% of peak while active): the unary
 # kernels are bound by the integer ALU pipe with the FP64 pipe close behind,
 # tadd by the FP64 pipe, tmul by the FP64 pipe and HBM together.
 PIPES = {"texp": {"alu_pct": 71.1, "fp64_pct": 69.5}, "texpm1": {"alu_pct": 74.1, "fp64_pct": 67.8},
-         "tlog": {"alu_pct": 77.5, "fp64_pct": 55.1}, "tlog1p": {"alu_pct": 74.7, "fp64_pct": 71.9},
+         "tlog": {"alu_pct": 77.5, "fp64_pct": 55.1}, "tlog1p": {"alu_pct": 78.8, "fp64_pct": 77.4},
          "tadd": {"alu_pct": 17.4, "fp64_pct": 83.1}, "tmul": {"alu_pct": 18.6, "fp64_pct": 93.4}}
 
 def parse():
