@@ -59,7 +59,7 @@ enum {
 
 /* Twofold exponent z0 + z1 = e^(x0 + x1).
  * Paper: "Twofold exponent" > "Algorithm summary", algorithms texp and texp0
- * (with pexp0 computed here by a k ln2 + j ln2/256 reduction, table and
+ * (with pexp0 computed here by a k ln2 + j ln2/65536 reduction, table and
  * Taylor polynomial in twofold arithmetic).  z0 = RN(e^x0): +Inf for
  * x0 >= 709.782712893384, subnormal below x0 = -708.396..., 0 at or below
  * x0 = -745.1332191019412. */
