@@ -16,6 +16,9 @@ tables, a stride of the large ones), from the definitions stated in the kernels:
   TF_FLOGT[i]       {c = RN_float(2048/i), -log c as a float pair, c - 1}
   TF_FT / TF_FE[j]  2^(j/512) and 2^(j/512) - 1 as float pairs
   TF_F_C0..C2       ln2/512 split, C0 with 7 bits;  TF_F_L0..L2  ln 2 split
+
+and replays the double exp core's FP64 reduction with exact rationals (its
+exactness and the bound on the reduced argument that the degree-6 H assumes).
 """
 import decimal
 import os
@@ -163,3 +166,35 @@ def test_float_tables():
         assert D(cm1) == D(c) - 1
         L = C.minus(C.ln(D(c)))
         assert abs(C.subtract(D(h) + D(l), L)) <= abs(L) * C.power(2, -47) + C.power(2, -80)
+
+
+def _fma(a, b, c):
+    """RN(a b + c) for doubles, from the exact rational value."""
+    from fractions import Fraction
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def test_exp_reduction_is_exact():
+    """The exp core's FP64 reduction (fx_reduce) as the kernel computes it,
+    replayed with exact rationals: N = RN(x 65536/ln2) from the low word of
+    fma(x, INV_C, 1.5 2^52), r0 = fma(-N, C0, x) is exactly x - N C0 (no
+    rounding), and r = x - N ln2/65536 stays below 2^-17.52 for x over the
+    clamped range [-746, 710] (random, near the thresholds, tiny)."""
+    from fractions import Fraction
+    inv_c = float.fromhex(_define("TF_INV_C"))
+    c0 = float.fromhex(_define("TF_C0"))
+    ln2_q = Fraction(C.multiply(LN2, C.power(2, 200)).to_integral_value()) / 2**200
+    shift = float.fromhex("0x1.8p52")
+    rng = np.random.default_rng(5)
+    xs = list(rng.uniform(-746.0, 710.0, 4000)) + list(np.exp2(rng.uniform(-60, 9.5, 2000)) * rng.choice([-1, 1], 2000))
+    xs += [-746.0, 710.0, -745.1332191019412, 709.782712893384, -708.3964185322641, 512.0, -512.0,
+           511.99999999999994, 2.0**-17, -(2.0**-17), 5e-324, 0.0]
+    for x in xs:
+        t = _fma(x, inv_c, shift)
+        n = int(t - shift)  # the low word of t, as __double2loint
+        nd = float(n)
+        assert nd == t - shift and abs(n) < 2**27
+        r0 = _fma(-nd, c0, x)
+        assert Fraction(r0) == Fraction(x) - Fraction(n) * Fraction(c0), x  # exact
+        r = Fraction(x) - n * ln2_q / 65536
+        assert abs(r) < Fraction(2) ** -17 * Fraction(0.6974), x  # 2^-17.52
