@@ -17,8 +17,9 @@ tables, a stride of the large ones), from the definitions stated in the kernels:
   TF_FT / TF_FE[j]  2^(j/512) and 2^(j/512) - 1 as float pairs
   TF_F_C0..C2       ln2/512 split, C0 with 7 bits;  TF_F_L0..L2  ln 2 split
 
-and replays the double exp core's FP64 reduction with exact rationals (its
-exactness and the bound on the reduced argument that the degree-6 H assumes).
+and replays two steps of the double exp core: its FP64 reduction with exact
+rationals (exactness, and the bound on the reduced argument that the degree-6
+H assumes) and that H itself bit for bit in integers (its error bound).
 """
 import decimal
 import math
