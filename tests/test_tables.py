@@ -17,9 +17,10 @@ tables, a stride of the large ones), from the definitions stated in the kernels:
   TF_FT / TF_FE[j]  2^(j/512) and 2^(j/512) - 1 as float pairs
   TF_F_C0..C2       ln2/512 split, C0 with 7 bits;  TF_F_L0..L2  ln 2 split
 
-and replays two steps of the double exp core: its FP64 reduction with exact
-rationals (exactness, and the bound on the reduced argument that the degree-6
-H assumes) and that H itself bit for bit in integers (its error bound).
+and replays three steps of the double kernels: the exp core's FP64 reduction
+with exact rationals (exactness, and the bound on the reduced argument that
+the degree-6 H assumes), that H bit for bit in integers (its error bound), and
+the logarithm's second table reduction in integers (its bound).
 """
 import decimal
 import math
@@ -244,3 +245,32 @@ def test_exp_core_H6_error_bound():
             got = Fraction(h6(A, neg), 1 << 127)
             worst = max(worst, abs(got - exact))
     assert worst < Fraction(1, 1 << 118), math.log2(worst)
+
+
+def test_log_second_reduction_replay():
+    """The logarithm's two table reductions (log_core, non-centre cells) replayed
+    in integers for random z in [sqrt(1/2), sqrt(2)): T1 = t1 2^136 exactly
+    from C_i, j = round(2^18 t1) from T1's top word as the kernel forms it, T2
+    = floor(|T1| C2_j / 2^24) (signed) + (C2_j - 2^24) 2^112; then |t2| <
+    2^-18.9 and T2 is within one unit of the exact ((1 + t1) c2_j - 1) 2^136."""
+    from fractions import Fraction
+    logt = _ints("TF_LOGT", 4)
+    log2t = _ints("TF_LOG2T", 4)
+    rng = np.random.default_rng(7)
+    zs = rng.uniform(0.70710678118654757, 1.4142135623730949, 20000)
+    for z in zs:
+        z = float(z)
+        i = min(max(int(round(1024 * z)), 724), 1448)
+        Ci = logt[i - 724][2]
+        T1 = int(Fraction(z) * Ci * 2**112) - 2**136  # t1 2^136 (exact: z has 53 bits)
+        assert Fraction(z) * Ci * 2**112 - 2**136 == T1
+        assert abs(T1) < 2**(136 - 10.4)
+        hi = T1 >> 64  # arithmetic
+        j = (hi + (1 << 53)) >> 54
+        assert -200 <= j <= 200
+        C2 = log2t[j + 200][2]
+        pr = (abs(T1) * C2) >> 24
+        T2 = (pr if T1 >= 0 else -pr) + (C2 - (1 << 24)) * 2**112
+        exact = (Fraction(T1, 2**136) + 1) * Fraction(C2, 2**24) - 1
+        assert abs(Fraction(T2, 2**136) - exact) <= Fraction(1, 2**136)
+        assert abs(T2) < 2**(136 - 18.9), (z, j)
