@@ -58,11 +58,14 @@ enum {
 };
 
 /* Twofold exponent z0 + z1 = e^(x0 + x1).
- * Paper: "Twofold exponent" > "Algorithm summary", algorithms texp and texp0
- * (with pexp0 computed here by a k ln2 + j ln2/65536 reduction, table and
- * Taylor polynomial in twofold arithmetic).  z0 = RN(e^x0): +Inf for
- * x0 >= 709.782712893384, subnormal below x0 = -708.396..., 0 at or below
- * x0 = -745.1332191019412. */
+ * Paper: "Twofold exponent" > "Algorithm summary", algorithms texp and texp0.
+ * The 2x-precise e^x0 (the paper's pexp0) is computed here by a reduction
+ * x0 = k ln2 + j ln2/65536 + r (N = 65536 k + j and the exact leading part of
+ * r in binary64), a 2^(j/65536) table and the Taylor polynomial of
+ * (e^r - 1)/r, the table product and the Taylor/Horner evaluation in exact
+ * 128-bit integer fixed point (not in twofold arithmetic), then the 2^k
+ * rescale in binary64.  z0 = RN(e^x0): +Inf for x0 >= 709.782712893384,
+ * subnormal below x0 = -708.396..., 0 at or below x0 = -745.1332191019412. */
 int tf_texp(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream);
 
 /* Twofold z0 + z1 = e^(x0 + x1) - 1.
@@ -72,9 +75,10 @@ int tf_texpm1(const double* x0, const double* x1, double* z0, double* z1, int64_
 
 /* Twofold logarithm z0 + z1 = log(y0 + y1).
  * Paper: "Twofold logarithm" > "Newton inversion" and "Algorithm summary"
- * (tlog, plog, tlog0): y0 = 2^n z, log z = -log c_i + log1p(z c_i - 1) with a
- * reciprocal table c_i, and one Newton step on e^x seeded by a 1x-precise
- * log1p of the reduced argument.
+ * (tlog, plog, tlog0): y0 = 2^n z, log z = -log c_i - log c2_j + log1p(t)
+ * with two reciprocal tables c_i, c2_j, and one Newton step on e^x seeded by a
+ * 1x-precise log1p of the reduced argument t (the reduction, seed, Newton step
+ * and final sum in exact 128-bit integer fixed point).
  * z0 = RN(log y0); y0 < 0 or NaN gives NaN, y0 = +-0 gives -Inf (z1 = 0).
  * y1 may be any double: a twofold that is not renormalised takes a slower
  * path in its warp. */
@@ -213,9 +217,12 @@ int tf_chain(const uint8_t* ops, const double* a0, const double* a1, const int64
  * The work-queue counter lives in a static device array of
  * TF_CHAIN_NOALLOC_SCRATCH bytes inside the library, which every GPU that
  * loads the library holds until the process exits.  This call allocates
- * nothing: the first call on each device looks up that device's address of
- * the array (cudaGetSymbolAddress, with the device current) and caches it, so
- * make that first call before any stream capture.  Every call clears the
+ * nothing: the first call in each CUDA context (normally once per device, in
+ * its primary context) looks up that context's address of the array
+ * (cudaGetSymbolAddress, with the device current) and caches it under the
+ * context's id, so make that first call before any stream capture.  After a
+ * cudaDeviceReset the device's new context gets a new id and the address is
+ * looked up again (the array starts over at another address).  Every call clears the
  * counter on `stream` and then uses it; all calls share the one array, so
  * calls whose work overlaps on the GPU (on different streams, or from
  * different host threads) race on it and give wrong results: keep them

@@ -128,7 +128,11 @@ struct OpLog1pF {
     __device__ static void eval(float a, float b, float& z0, float& z1) { tff::tlog1pf_impl<true>(a, b, z0, z1); }
 };
 
-__device__ __forceinline__ double2 ld2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
+// Inputs are read with ordinary (coherent) loads: the ABI lets z0 be x0 and z1
+// be x1, so an input array may be written during the launch, which rules out
+// the read-only (non-coherent) path and __restrict__ on the inputs.  Each
+// thread reads its elements before it writes them.
+__device__ __forceinline__ double2 ld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
 __device__ __forceinline__ void st2(double* p, double a, double b) {
     __stcs(reinterpret_cast<double2*>(p), make_double2(a, b));  // streaming: outputs are not re-read
 }
@@ -148,8 +152,8 @@ struct OpThreads<Op, decltype((void)Op::threads)> {
 
 // Unary, 2 elements per thread, 128-bit I/O.  Thread t covers elements 2t, 2t+1.
 template <class Op>
-__global__ void __launch_bounds__(OpThreads<Op>::value, Op::min_blocks) unary_v2(const double* __restrict__ x0,
-                                                     const double* __restrict__ x1, double* z0, double* z1, int64_t n) {
+__global__ void __launch_bounds__(OpThreads<Op>::value, Op::min_blocks) unary_v2(const double* x0, const double* x1,
+                                                                                     double* z0, double* z1, int64_t n) {
     int64_t t = (int64_t)blockIdx.x * OpThreads<Op>::value + threadIdx.x;
     int64_t i = 2 * t;
     double a0 = Op::dummy, a1 = Op::dummy, b0 = 0.0, b1 = 0.0;
@@ -198,15 +202,15 @@ __global__ void __launch_bounds__(kThreads) unary_v1(const double* x0, const dou
 
 // Float twofolds: 4 elements per thread, 128-bit loads and stores.
 template <class Op>
-__global__ void __launch_bounds__(kThreads) unary_f4(const float* __restrict__ x0, const float* __restrict__ x1,
-                                                     float* z0, float* z1, int64_t n) {
+__global__ void __launch_bounds__(kThreads) unary_f4(const float* x0, const float* x1, float* z0, float* z1,
+                                                     int64_t n) {
     int64_t i = 4 * ((int64_t)blockIdx.x * kThreads + threadIdx.x);
     float a[4], b[4], r[4], s[4];
     bool full = i + 3 < n;
     if (full) {
-        float4 v = __ldg(reinterpret_cast<const float4*>(x0 + i));
+        float4 v = *reinterpret_cast<const float4*>(x0 + i);
         a[0] = v.x, a[1] = v.y, a[2] = v.z, a[3] = v.w;
-        float4 w = x1 ? __ldg(reinterpret_cast<const float4*>(x1 + i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 w = x1 ? *reinterpret_cast<const float4*>(x1 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
         b[0] = w.x, b[1] = w.y, b[2] = w.z, b[3] = w.w;
     } else {
 #pragma unroll
@@ -249,9 +253,8 @@ __global__ void __launch_bounds__(kThreads) unary_f1(const float* x0, const floa
 }
 
 template <class Op>
-__global__ void __launch_bounds__(kThreads) binary_v2(const double* __restrict__ x0, const double* __restrict__ x1,
-                                                      const double* __restrict__ y0, const double* __restrict__ y1,
-                                                      double* z0, double* z1, int64_t n) {
+__global__ void __launch_bounds__(kThreads) binary_v2(const double* x0, const double* x1, const double* y0,
+                                                      const double* y1, double* z0, double* z1, int64_t n) {
     int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     int64_t i = 2 * t;
     if (i + 1 < n) {

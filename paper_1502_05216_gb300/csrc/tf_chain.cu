@@ -298,11 +298,23 @@ __global__ void __launch_bounds__(256) chain_step_kernel(const int32_t* __restri
     }
 }
 
-int launch_status() {
-    cudaError_t e = cudaGetLastError();
+// Error code of a failed (or successful) CUDA runtime call.  A failed call is
+// never TF_OK.
+int cuda_code(cudaError_t e) {
     if (e == cudaSuccess) return TF_OK;
     if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return TF_ERR_NODEVICE;
     return TF_ERR_LAUNCH;
+}
+
+// Status after a launch: the launch's own error, read (and cleared) once.
+int launch_status() { return cuda_code(cudaGetLastError()); }
+
+// Status of a runtime call that returned e: its error code (the call's error
+// is also cleared from the runtime's last-error slot, so that a later
+// launch_status reports only that launch).
+int call_status(cudaError_t e) {
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_code(e);
 }
 
 inline bool al8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
@@ -310,30 +322,80 @@ inline bool al8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 
 // Scratch of tf_chain_noalloc: the work-queue counter lives in this array,
 // which every device that loads the library holds until the process exits.
 // Host code must not pass the symbol itself to a kernel (on the host it only
-// stands for the device array); each device's address is looked up once.
+// stands for the device array); its device address is looked up instead.
 constexpr int kNoAllocScratchBytes = TF_CHAIN_NOALLOC_SCRATCH;
 static __device__ __align__(256) unsigned char g_chain_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
+// The address is looked up once per CUDA context (with that context current)
+// and cached under the context's id, which the driver never reuses within a
+// process: a context that is destroyed and created again (cudaDeviceReset)
+// loads the module again, possibly at another address, and gets a new id, so
+// a stale address is never used.  The id comes from the driver's cuCtxGetId
+// through the runtime's entry-point query (the library does not link the
+// driver library itself).  Without that entry point every call looks the
+// address up.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+constexpr int kCacheSlots = 64;
 std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void* addr;
+};
+ScratchSlot g_scratch_cache[kCacheSlots] = {};
+int g_scratch_next = 0;
+bool g_entry_tried = false;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
 
-// Device address of g_chain_scratch on the current device, looked up with
-// cudaGetSymbolAddress on the first call per device and cached.
+// Id of the current context, or 0 if it cannot be had.
+unsigned long long current_ctx_id() {
+    if (!g_entry_tried) {
+        g_entry_tried = true;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+            g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of g_chain_scratch in the current device's context.
 int noalloc_scratch(void** out) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return launch_status() == TF_OK ? TF_ERR_NODEVICE : launch_status();
-    if (dev < 0 || dev >= kMaxDevices) return TF_ERR_ARG;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return call_status(e);
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_chain_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();  // do not leave the error for an unrelated later check
-            return TF_ERR_LAUNCH;
+    unsigned long long id = current_ctx_id();
+    if (id != 0) {
+        for (int k = 0; k < kCacheSlots; ++k) {
+            if (g_scratch_cache[k].ctx_id == id) {
+                *out = g_scratch_cache[k].addr;
+                return TF_OK;
+            }
         }
-        g_scratch_addr[dev] = p;
     }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_chain_scratch);
+    if (e != cudaSuccess) return call_status(e);
+    if (!p) return TF_ERR_LAUNCH;
+    if (id == 0) id = current_ctx_id();  // the lookup made the device's context current
+    if (id != 0) {
+        g_scratch_cache[g_scratch_next] = {id, p};
+        g_scratch_next = (g_scratch_next + 1) % kCacheSlots;
+    }
+    *out = p;
     return TF_OK;
 }
 
@@ -354,20 +416,22 @@ int tf_chain(const uint8_t* ops, const double* a0, const double* a1, const int64
         return TF_ERR_ALIGN;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, chain_fused) != cudaSuccess) return launch_status() == TF_OK ? TF_ERR_LAUNCH : launch_status();
+    cudaError_t e = cudaFuncGetAttributes(&fa, chain_fused);
+    if (e != cudaSuccess) return call_status(e);
     if (threads > fa.maxThreadsPerBlock) return TF_ERR_ARG;  // the kernel's registers do not fit
     if (blocks <= 0) {
         int dev = 0, sms = 0, per_sm = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain_fused, threads, 0) != cudaSuccess)
-            return launch_status() == TF_OK ? TF_ERR_LAUNCH : launch_status();
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain_fused, threads, 0);
+        if (e != cudaSuccess) return call_status(e);
         blocks = sms * (per_sm > 0 ? per_sm : 1);
     }
     // more warps than tasks would idle (a task has at least one chain)
     int64_t need = (n_chains + threads / 32 - 1) / (threads / 32);
     if (blocks > need) blocks = (int)need;
-    if (cudaMemsetAsync(workspace, 0, sizeof(unsigned long long), s) != cudaSuccess) return launch_status();
+    e = cudaMemsetAsync(workspace, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return call_status(e);
     chain_fused<<<blocks, threads, 0, s>>>(ops, a0, a1, step_base, len, s0, s1, n_chains, max_len, group,
                                            static_cast<unsigned long long*>(workspace));
     return launch_status();

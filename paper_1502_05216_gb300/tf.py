@@ -106,7 +106,8 @@ def _unary(name, x0, x1=None, out=None, stream=None):
         out = (torch.empty_like(x0), torch.empty_like(x0))
     args = (_ptr(x0, "x0", n, dev), _ptr(x1, "x1", n, dev), _ptr(out[0], "z0", n, dev),
             _ptr(out[1], "z1", n, dev))
-    _check(getattr(load(), "tf_" + name)(*args, n, _stream(stream, dev)), name)
+    with torch.cuda.device(dev):
+        _check(getattr(load(), "tf_" + name)(*args, n, _stream(stream, dev)), name)
     return out
 
 
@@ -119,7 +120,8 @@ def _unary_f(name, x0, x1=None, out=None, stream=None):
     f32 = torch.float32
     args = (_ptr(x0, "x0", n, dev, f32), _ptr(x1, "x1", n, dev, f32), _ptr(out[0], "z0", n, dev, f32),
             _ptr(out[1], "z1", n, dev, f32))
-    _check(getattr(load(), "tf_" + name + "f")(*args, n, _stream(stream, dev)), name + "f")
+    with torch.cuda.device(dev):
+        _check(getattr(load(), "tf_" + name + "f")(*args, n, _stream(stream, dev)), name + "f")
     return out
 
 
@@ -131,7 +133,8 @@ def _binary(name, x0, x1, y0, y1, out=None, stream=None):
         out = (torch.empty_like(x0), torch.empty_like(x0))
     args = (_ptr(x0, "x0", n, dev), _ptr(x1, "x1", n, dev), _ptr(y0, "y0", n, dev), _ptr(y1, "y1", n, dev),
             _ptr(out[0], "z0", n, dev), _ptr(out[1], "z1", n, dev))
-    _check(getattr(load(), "tf_" + name)(*args, n, _stream(stream, dev)), name)
+    with torch.cuda.device(dev):
+        _check(getattr(load(), "tf_" + name)(*args, n, _stream(stream, dev)), name)
     return out
 
 
@@ -273,8 +276,9 @@ def chain(ops, a0, a1, step_base, length, s0, s1, max_len, workspace, threads=12
             _dptr(s1, "s1", torch.float64, dev))
     if not workspace.is_cuda or workspace.device != dev:
         raise TypeError(f"workspace must be on {dev}")
-    _check(load().tf_chain(*args, n, int(max_len), workspace.data_ptr(), int(threads), int(blocks), int(group),
-                           _stream(stream, dev)), "chain")
+    with torch.cuda.device(dev):
+        _check(load().tf_chain(*args, n, int(max_len), workspace.data_ptr(), int(threads), int(blocks),
+                               int(group), _stream(stream, dev)), "chain")
 
 
 def chain_noalloc(ops, a0, a1, step_base, length, s0, s1, max_len, threads=128, blocks=0, group=0,
@@ -291,8 +295,11 @@ def chain_noalloc(ops, a0, a1, step_base, length, s0, s1, max_len, threads=128, 
             _dptr(a1, "a1", torch.float64, dev), _dptr(step_base, "step_base", torch.int64, dev),
             _dptr(length, "length", torch.int32, dev), _dptr(s0, "s0", torch.float64, dev),
             _dptr(s1, "s1", torch.float64, dev))
-    _check(load().tf_chain_noalloc(*args, n, int(max_len), int(threads), int(blocks), int(group),
-                                   _stream(stream, dev)), "chain_noalloc")
+    # the library finds the static scratch of the current device: make s0's
+    # device current for the call
+    with torch.cuda.device(dev):
+        _check(load().tf_chain_noalloc(*args, n, int(max_len), int(threads), int(blocks), int(group),
+                                       _stream(stream, dev)), "chain_noalloc")
 
 
 def chain_step(op, idx, step_base_t, a0, a1, s0, s1, stream=None):
@@ -302,7 +309,8 @@ def chain_step(op, idx, step_base_t, a0, a1, s0, s1, stream=None):
     args = (_dptr(idx, "idx", torch.int32, dev), idx.numel(), int(step_base_t),
             _dptr(a0, "a0", torch.float64, dev), _dptr(a1, "a1", torch.float64, dev),
             _dptr(s0, "s0", torch.float64, dev), _dptr(s1, "s1", torch.float64, dev))
-    _check(load().tf_chain_step(int(op), *args, _stream(stream, dev)), "chain_step")
+    with torch.cuda.device(dev):
+        _check(load().tf_chain_step(int(op), *args, _stream(stream, dev)), "chain_step")
 
 
 FUNCS = {"texp": texp, "texpm1": texpm1, "tlog": tlog, "tlog1p": tlog1p, "tadd": tadd, "tmul": tmul}
@@ -393,7 +401,8 @@ def call_host_zero_copy(name, *host_arrays, out=None, device="cuda", stream=None
     args = [_pinned_ptr(a, nm, n) for a, nm in zip(h, names)] + [_pinned_ptr(out[0], "z0", n),
                                                                  _pinned_ptr(out[1], "z1", n)]
     st = stream if stream is not None else torch.cuda.current_stream(dev)
-    _check(getattr(load(), "tf_" + name)(*args, n, st.cuda_stream), name)
+    with torch.cuda.device(dev):
+        _check(getattr(load(), "tf_" + name)(*args, n, st.cuda_stream), name)
     st.synchronize()
     return out
 

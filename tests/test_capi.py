@@ -68,17 +68,16 @@ def test_error_codes_before_any_launch(lib):
         assert f(good, good, None, good, good, good, 3, None) == 1
         assert f(good, good, good, odd, good, good, 3, None) == 3
     # chains: sizes, block size and op code are checked first
-    vp = ctypes.c_void_p
-    lib.tf_chain.argtypes = [vp] * 7 + [ctypes.c_int64, ctypes.c_int32, vp, ctypes.c_int, ctypes.c_int, vp]
-    lib.tf_chain_step.argtypes = [ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int64] + [vp] * 5
+    # (tf.load() declared the argument types of every entry point)
     g7 = [good] * 7
-    assert lib.tf_chain(*g7, 0, 5, good, 128, 0, None) == 0         # no chains: no-op
-    assert lib.tf_chain(*g7, -1, 5, good, 128, 0, None) == 2        # TF_ERR_SIZE
-    assert lib.tf_chain(*g7, 10, -1, good, 128, 0, None) == 2
-    assert lib.tf_chain(*g7, 10, 5, good, 33, 0, None) == 6         # TF_ERR_ARG: not a warp multiple
-    assert lib.tf_chain(*g7, 10, 5, good, 2048, 0, None) == 6
-    assert lib.tf_chain(*g7, 10, 5, None, 128, 0, None) == 1        # no workspace
-    assert lib.tf_chain(*g7, 10, 5, odd, 128, 0, None) == 3
+    assert lib.tf_chain(*g7, 0, 5, good, 128, 0, 0, None) == 0      # no chains: no-op
+    assert lib.tf_chain(*g7, -1, 5, good, 128, 0, 0, None) == 2     # TF_ERR_SIZE
+    assert lib.tf_chain(*g7, 10, -1, good, 128, 0, 0, None) == 2
+    assert lib.tf_chain(*g7, 10, 5, good, 33, 0, 0, None) == 6      # TF_ERR_ARG: not a warp multiple
+    assert lib.tf_chain(*g7, 10, 5, good, 2048, 0, 0, None) == 6
+    assert lib.tf_chain(*g7, 10, 5, good, 128, 0, 33, None) == 6    # TF_ERR_ARG: group
+    assert lib.tf_chain(*g7, 10, 5, None, 128, 0, 0, None) == 1     # no workspace
+    assert lib.tf_chain(*g7, 10, 5, odd, 128, 0, 0, None) == 3
     assert lib.tf_chain_step(7, good, 5, 0, good, good, good, good, None) == 6
     assert lib.tf_chain_step(0, good, 0, 0, good, good, good, good, None) == 0
     assert lib.tf_chain_step(1, good, -2, 0, good, good, good, good, None) == 2
@@ -95,3 +94,23 @@ def test_binding_has_no_cpu_fallback():
     x = torch.zeros(4, dtype=torch.float64)
     with pytest.raises(TypeError):
         tf.texp(x, x)
+
+
+def test_failed_cuda_call_is_never_ok(lib):
+    """With no usable CUDA device, calls whose arguments pass the checks reach
+    the CUDA runtime, which fails; the entry points must report that failure
+    (TF_ERR_NODEVICE or TF_ERR_LAUNCH), also when called a second time (the
+    runtime clears a non-sticky error when it is read).  Runs only where no
+    CUDA device is visible: the pointers are fake, and nothing may be launched
+    on them."""
+    import torch
+    if torch.cuda.is_available() or torch.cuda.device_count() > 0:
+        pytest.skip("a CUDA device is visible: the fake pointers must not reach a launch")
+    good = ctypes.c_void_p(1 << 20)
+    g7 = [good] * 7
+    for _ in range(2):
+        assert lib.tf_chain(*g7, 10, 5, good, 128, 0, 0, None) in (4, 5)
+        assert lib.tf_chain(*g7, 10, 5, good, 128, 64, 0, None) in (4, 5)
+        assert lib.tf_chain_noalloc(*g7, 10, 5, 128, 0, 0, None) in (4, 5)
+        assert lib.tf_texp(good, good, good, good, 5, None) in (4, 5)
+        assert lib.tf_chain_step(0, good, 5, 0, good, good, good, good, None) in (4, 5)

@@ -71,7 +71,29 @@ def test_noalloc_equals_workspace_entry_point_twice(lib):
         assert np.all(err <= 2.0**-97 * K * np.abs(Fh) + 2.0**-1060), f"call {k + 1}: beyond 2^-97 K |F|"
 
 
+def test_noalloc_binding_equals_chain(lib):
+    """The Python binding tf.chain_noalloc (which makes the tensors' device
+    current for the call) against tf.chain, bit for bit, twice."""
+    import torch
+    from paper_1502_05216_gb300 import tf
+    batch = I.chains(3000, seed=53, mean_len=40.0, cap=200)
+    d = _device_batch(batch)
+    ws = torch.zeros(tf.CHAIN_WORKSPACE, dtype=torch.uint8, device="cuda:0")
+    for k in range(2):
+        r0, r1 = d["s0"].clone(), d["s1"].clone()
+        g0, g1 = d["s0"].clone(), d["s1"].clone()
+        common = (d["ops"], d["a0"], d["a1"], d["sb"], d["len"])
+        tf.chain(*common, r0, r1, int(batch["max_len"]), ws)
+        tf.chain_noalloc(*common, g0, g1, int(batch["max_len"]))
+        torch.cuda.synchronize()
+        assert torch.equal(r0.view(torch.int64), g0.view(torch.int64)), f"call {k + 1}: z0"
+        assert torch.equal(r1.view(torch.int64), g1.view(torch.int64)), f"call {k + 1}: z1"
+
+
 def test_noalloc_rejects_bad_arguments(lib):
+    # The pointers below are fake: every case must be rejected by the argument
+    # checks, which come before any device access (the scratch lookup, the
+    # memset and the launch), or return early with nothing to do.
     good = ctypes.c_void_p(1 << 20)
     g7 = [good] * 7
     assert lib.tf_chain_noalloc(*g7, (1 << 40) + 1, 5, 128, 0, 0, None) == 2  # beyond the maximum: TF_ERR_SIZE
