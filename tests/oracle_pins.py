@@ -15,7 +15,10 @@ What the oracle is pinned to:
     exp(twofold k ln 2) = 2^k, log(2^k) = k ln 2 (ln 2 from tests/golden);
   * invariants: monotonicity of Z0, exp(x) exp(-x) = 1, Z0 independent of x1,
     log(exp(x)) = x, log1p(y) = log(1 + y) when 1 + y is exact;
-  * the special-value rules (NaN, infinities, overflow/underflow).
+  * the special-value rules (NaN, infinities, overflow/underflow);
+  * arguments whose f(x0) lies next to a rounding midpoint, from the Taylor
+    series (the binary128 step flags them and a decimal re-decision runs),
+    and the re-decision and rounding helpers on constructed cases.
 """
 from __future__ import annotations
 
@@ -493,7 +496,136 @@ def pin_coupled_decimal(lib):
     return fails
 
 
+# Arguments whose f(x0) lies next to the midpoint of two adjacent doubles,
+# found from the Taylor series (not by search): the second-order term of the
+# series lands exactly on the half spacing and the third-order term, 2^-50 of a
+# spacing or less away from it, decides the rounding.  The expected main part
+# is written from that reading of the series; the pin checks it against decimal
+# too.  Each lies within 2^-50 of a spacing of the midpoint, so the binary128
+# step flags it and the oracle's decimal re-decision runs on it.
+NEAR_MIDPOINT = [
+    # f, x0, RN(f(x0)): series and midpoint
+    ("texp", 2.0**-53, 1.0 + 2.0**-52),            # 1 + 2^-53 + 2^-107 + ..: above the midpoint 1 + 2^-53
+    ("texp", -(2.0**-54), 1.0),                    # 1 - 2^-54 + 2^-109 - ..: above the midpoint 1 - 2^-54
+    ("texpm1", 2.0**-52, 2.0**-52 + 2.0**-104),    # 2^-52 + 2^-105 + 2^-158.6: above 2^-52 + 2^-105
+    ("texpm1", -(2.0**-53), -(2.0**-53)),          # -2^-53 + 2^-107 - 2^-161.6: beyond -(2^-53 - 2^-107)
+    ("tlog", 1.0 - 2.0**-52, -(2.0**-52 + 2.0**-104)),   # -2^-52 - 2^-105 - 2^-157.6
+    ("tlog1p", -(2.0**-52), -(2.0**-52 + 2.0**-104)),    # the same value
+    ("tlog1p", 2.0**-53, 2.0**-53),                # 2^-53 - 2^-107 + 2^-160.6: above 2^-53 - 2^-107
+]
+
+
+def _rn_double_exact(v: decimal.Decimal) -> float:
+    """Nearest double of a decimal value by exact rational division (Python's
+    int / int true division is correctly rounded), independent of the oracle's
+    own rounding helpers."""
+    f = Fraction(v)
+    return f.numerator / f.denominator
+
+
+def _raw(lib, func, x0, x1=None, f32=False):
+    """The binary128 step alone (before any re-decision): Z0, Gh, Gl, flags."""
+    import ctypes
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    x1 = None if x1 is None else np.ascontiguousarray(x1, dtype=np.float64)
+    n = x0.shape[0]
+    Z0, Gh, Gl, A = (np.empty(n) for _ in range(4))
+    fl = np.empty(n, dtype=np.uint32)
+    dp = lambda a: None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    rc = lib.tfo_eval2(oracle.KINDS[func], int(f32), n, dp(x0), dp(x1), None, None, dp(Z0), dp(Gh), dp(Gl),
+                       dp(A), fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint)))
+    assert rc == 0
+    return Z0, Gh, Gl, fl
+
+
+@_hiprec
+def pin_near_midpoint(lib):
+    """Arguments whose f(x0) lies within 2^-50 of a spacing of a rounding
+    midpoint (NEAR_MIDPOINT): the binary128 step flags each one; the oracle's
+    answer has the main part the series fixes, equal to the decimal value
+    rounded by exact rational division, and Gh + Gl = F - Z0 in decimal for
+    x1 = 0 and two small x1.  The re-decision itself is then checked on a
+    binary128 main part that landed on the wrong side of the midpoint (one
+    spacing off, with G moved to keep Z0 + G = F): it must return the right
+    main part and keep Z0 + G = F (a wrong shift of G moves F by a whole
+    spacing).  Finally the rounding helpers that the re-decision uses must
+    round exact midpoints to even and their neighbours to nearest."""
+    fails = []
+    c = _ctx(80)
+    for func, x, want in NEAR_MIDPOINT:
+        x0 = np.array([x, x, x])
+        x1 = np.array([0.0, x * 2.0**-60, -x * 2.0**-57])
+        Z0c, Ghc, Glc, fl = _raw(lib, func, x0, x1)
+        if not all(fl & oracle.FL_AMBIG):
+            fails.append(f"{func}({x!r}): not flagged as near a midpoint")
+        dec = _rn_double_exact(dec_eval(func, _D(x), 80))
+        if dec != want:
+            fails.append(f"{func}({x!r}): decimal rounds to {dec!r}, the series to {want!r}")
+        r = oracle.evaluate(func, x0, x1, lib=lib)
+        for i in range(3):
+            if r.Z0[i] != want:
+                fails.append(f"{func}({x!r}): Z0 = {r.Z0[i]!r}, want {want!r}")
+                continue
+            F = dec_eval(func, c.add(_D(x0[i]), _D(x1[i])), 70)
+            if not _close(r.Gh[i], r.Gl[i], c.subtract(F, _D(want)), F):
+                fails.append(f"{func}({x!r}+{x1[i]!r}): G = {r.Gh[i]!r} + {r.Gl[i]!r}")
+        # a main part on the wrong side of the midpoint: the spacing step of
+        # the true value's binade toward the other neighbour
+        other = float(np.nextafter(want, -np.inf if dec_eval(func, _D(x), 80) < _D(want) else np.inf))
+        other = other if other != want else float(np.nextafter(want, np.inf))
+        F0 = Fraction(float(Z0c[0])) + Fraction(float(Ghc[0])) + Fraction(float(Glc[0]))
+        if float(Z0c[0]) == want:
+            # move the binary128 answer to the other neighbour, keeping F
+            Z0s = np.array([other])
+            Ghs = np.array([float(Fraction(float(Ghc[0])) + Fraction(want) - Fraction(other))])
+        else:
+            Z0s, Ghs = Z0c[:1].copy(), Ghc[:1].copy()
+        fls = np.array([oracle.FL_AMBIG], dtype=np.uint32)
+        oracle.redecide(func, x0[:1], Z0s, Ghs, fls)
+        F1 = Fraction(float(Z0s[0])) + Fraction(float(Ghs[0])) + Fraction(float(Glc[0]))
+        if Z0s[0] != want:
+            fails.append(f"re-decision of {func}({x!r}): Z0 = {Z0s[0]!r}, want {want!r}")
+        if abs(F1 - F0) > abs(F0) * Fraction(1, 2**100):
+            fails.append(f"re-decision of {func}({x!r}) moved Z0 + G by {float(F1 - F0)!r}")
+    # rounding helpers: exact midpoints go to even, a hair off goes to nearest
+    # (the decimal sums below are exact at 2000 digits: a subnormal double has
+    # up to 751 significant digits)
+    with decimal.localcontext(decimal.Context(prec=2000, Emax=999999, Emin=-999999)):
+        fails += _rounding_helper_checks()
+    return fails
+
+
+def _rounding_helper_checks():
+    fails = []
+    D = decimal.Decimal
+    for lo in (1.0, 1.0 + 2.0**-52, 2.0**-1074, 3 * 2.0**-1074, 0.75, 2.0**1023 * 1.5):
+        hi = float(np.nextafter(lo, np.inf))
+        mid = (D(lo) + D(hi)) / 2
+        even = lo if (np.array(lo).view(np.int64) & 1) == 0 else hi
+        eps = (D(hi) - D(lo)) * D(2) ** -60
+        for sgn in (1, -1):
+            for v, w in ((mid, even), (mid + eps, hi), (mid - eps, lo)):
+                got = oracle.round_to_double(sgn * v)
+                if got != sgn * w:
+                    fails.append(f"round_to_double({sgn * v:.25e}) = {got!r}, want {sgn * w!r}")
+    for lo in (np.float32(1.0), np.float32(1.0) + np.float32(2.0**-23), np.float32(2.0**-149), np.float32(0.75)):
+        hi = np.nextafter(lo, np.float32(np.inf))
+        mid = (D(float(lo)) + D(float(hi))) / 2
+        even = lo if (np.array(lo).view(np.int32) & 1) == 0 else hi
+        eps = (D(float(hi)) - D(float(lo))) * D(2) ** -60
+        for sgn in (1, -1):
+            for v, w in ((mid, even), (mid + eps, hi), (mid - eps, lo)):
+                got = oracle.round_to_float(sgn * v)
+                if got != sgn * float(w):
+                    fails.append(f"round_to_float({sgn * v:.25e}) = {got!r}, want {sgn * float(w)!r}")
+    if oracle.round_to_double(D(2) ** 1024 - D(2) ** 970) != math.inf:
+        fails.append("round_to_double: 2^1024 - 2^970 must overflow")
+    if oracle.round_to_double(D(2) ** 1024 - D(2) ** 970 - 1) != 1.7976931348623157e308:
+        fails.append("round_to_double: just below 2^1024 - 2^970 must give the largest double")
+    return fails
+
+
 ALL_PINS = [pin_mainpart_decimal, pin_deviation_decimal, pin_closed_forms, pin_series,
             pin_invariants, pin_special, pin_arith, pin_cancellation, pin_chain_decimal,
             pin_chain_condition, pin_mainpart_decimal_f32, pin_deviation_decimal_f32,
-            pin_coupled_decimal]
+            pin_coupled_decimal, pin_near_midpoint]

@@ -22,3 +22,17 @@ def test_planted_mistake_is_caught(k):
             caught.append(pin.__name__)
             break
     assert caught, f"planted mistake {k} ({PLANTS[k]}) passed every pin"
+
+
+PY_PLANTS = {11: "re-decision shifts the deviation the wrong way", 12: "re-decision rounds toward zero"}
+
+
+@pytest.mark.parametrize("k", sorted(PY_PLANTS), ids=lambda k: PY_PLANTS[k].replace(" ", "_"))
+def test_planted_redecision_mistake_is_caught(k, monkeypatch):
+    """Mistakes planted in the oracle's decimal re-decision of main parts near a
+    rounding midpoint: the near-midpoint pin family catches them, and it is the
+    only family that reaches that code with a main part to change."""
+    lib = oracle.load()
+    monkeypatch.setattr(oracle, "_PLANT", k)
+    caught = [pin.__name__ for pin in P.ALL_PINS if pin(lib)]
+    assert caught == ["pin_near_midpoint"], f"planted mistake {k} ({PY_PLANTS[k]}) caught by {caught}"
