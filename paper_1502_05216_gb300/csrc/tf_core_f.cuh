@@ -165,10 +165,12 @@ __device__ __forceinline__ float clamp_exp_arg(float x) {
     return x;
 }
 
-// e (x1 + x1^2/2) + c, x1 small (|x1| < 2^-15: the x1^3 term is below 2^-47 |x1|).
-__device__ __forceinline__ float add_pert(float e, float x1, float c) {
-    float p = mul(e, x1);
-    return fma_rn(e, x1, fma_rn(p, mul(0.5f, x1), c));
+// (z + e)(x1 + x1^2/2) + c for e^x0 = z + e (z its leading float, e the rest)
+// and a small x1 (|x1| < 2^-15: the x1^3/6 term is below 2^-47.6 e^x0): t = z
+// x1/2 + e, then t x1 + c, then z x1 + that, the large term rounded once.
+__device__ __forceinline__ float add_pert(float z, float e, float x1, float c) {
+    float t = fma_rn(z, mul(0.5f, x1), e);
+    return fma_rn(z, x1, fma_rn(t, x1, c));
 }
 __device__ __forceinline__ bool pert_is_large(float x1) { return absbits(x1) >= 0x38000000u; }  // 2^-15
 __device__ __forceinline__ bool pert_is_loose(float x1) { return absbits(x1) > 0x3eae0000u; }   // 0.33984
@@ -178,8 +180,11 @@ static __device__ __noinline__ ff expm1_pair_f(float x1) {
     return {expm1f(x1), 0.0f};
 }
 
+// kPair: the 2x-precise e^x1 - 1 for every finite x1 (texpm1f, whose result
+// may be as small as x1 itself).
+template <bool kPair = false>
 __device__ __forceinline__ float pert_term(float eh, float el, float x1, float c) {
-    if (!pert_is_large(x1)) return fma_rn(eh, x1, fma_rn(el, x1, fma_rn(eh, mul(mul(0.5f, x1), x1), c)));
+    if (!kPair && !pert_is_large(x1)) return fma_rn(eh, x1, fma_rn(el, x1, fma_rn(eh, mul(mul(0.5f, x1), x1), c)));
     if (absbits(x1) >= kExpMask) return (x1 > 0.0f) ? x1 : sub(sub(c, el), eh);
     ff t = expm1_pair_f(x1);
     return fma_rn(eh, t.hi, fma_rn(el, t.hi, fma_rn(eh, t.lo, c)));
@@ -215,7 +220,9 @@ static __device__ __noinline__ float loose_deviation_f(float x0, float x1, float
     float w0, w1;
     if constexpr (kExpm1) texpm1f_impl<false, false>(s.hi, slo, w0, w1);
     else texpf_impl<false, false>(s.hi, slo, w0, w1);
-    return (absbits(w0) == kExpMask) ? w0 : add(sub(w0, z0), w1);
+    if (absbits(w0) == kExpMask) return w0;
+    ff d = two_sum(w0, -z0);  // w0 - z0 exactly
+    return add(d.hi, add(d.lo, w1));
 }
 
 // ---------------------------------------------------------------------------
@@ -242,7 +249,7 @@ static __device__ __noinline__ void texpf_rare(float x0, float x1, float zA, flo
             return;
         }
     }
-    z1 = pert_term(z0, 0.0f, x1, e);
+    z1 = pert_term(z0, e, x1, e);  // e^x0 = z0 + e
 }
 
 template <bool kVote, bool kTop>
@@ -250,7 +257,7 @@ __device__ __forceinline__ void texpf_impl(float x0, float x1, float& z0, float&
     ExpCoreF c = exp_core_f(clamp_exp_arg(x0));
     float sk = from_bits((uint32_t)(c.k + 127) << 23);  // 2^k for -126 <= k <= 127; other k are rare
     z0 = mul(c.zA, sk);
-    z1 = mul(add_pert(c.zA, x1, c.eA), sk);  // one rounding into a subnormal z1
+    z1 = mul(add_pert(c.zA, c.eA, x1, c.eA), sk);  // one rounding into a subnormal z1
     bool rare = (c.k < -125) | (c.k > 127) | pert_is_large(x1);
     if (warp_any<kVote>(rare)) {
         if (rare) texpf_rare<kTop>(x0, x1, c.zA, c.eA, c.k, z0, z1);
@@ -277,7 +284,7 @@ static __device__ __noinline__ void texpm1f_rare(float x0, float x1, float vh, f
         z0 = mul(mul(vh, sh), 0x1p64f);
         e = mul(mul(vl, sh), 0x1p64f);
         exh = z0;
-        exl = 0.0f;
+        exl = e;
     } else {
         ff s = two_sum(1.0f, z0);
         exh = s.hi;
@@ -290,7 +297,15 @@ static __device__ __noinline__ void texpm1f_rare(float x0, float x1, float vh, f
             return;
         }
     }
-    z1 = pert_term(exh, exl, x1, e);
+    z1 = pert_term<true>(exh, exl, x1, e);
+}
+
+// |x1| >= 2^-16 min(1, |x0|) (exponent fields): texpm1f's second-order term
+// could then miss 2^-44 of the result, and the lane takes the rare path.
+__device__ __forceinline__ bool pert_is_large_m1(float x0, float x1) {
+    uint32_t a = min(absbits(x0), 0x3f800000u);
+    uint32_t thr = (a > (16u << 23)) ? ((a & kExpMask) - (16u << 23)) : 0u;
+    return absbits(x1) > thr;
 }
 
 template <bool kVote, bool kTop>
@@ -323,9 +338,9 @@ __device__ __forceinline__ void texpm1f_impl(float x0, float x1, float& z0, floa
     float sc = kpos ? sk : 1.0f;
     z0 = mul(W.hi, sc);
     float zl = mul(W.lo, sc);
-    float ex = add(add(1.0f, z0), zl);  // e^x0 to 1x
-    z1 = add_pert(ex, x1, zl);
-    bool rare = (k > 127) | pert_is_large(x1);
+    ff ex = sorted_two_sum(1.0f, z0);  // e^x0 = ex.hi + ex.lo + zl
+    z1 = add_pert(ex.hi, add(ex.lo, zl), x1, zl);
+    bool rare = (k > 127) | pert_is_large_m1(x0, x1);
     if (warp_any<kVote>(rare)) {
         if (rare) texpm1f_rare<kTop>(x0, x1, V.hi, V.lo, zl, k, z0, z1);
     }

@@ -71,8 +71,9 @@ def _check_coupled(tf, func, x0, x1, where):
     assert np.array_equal(z0[keep].view(np.int64), w0[keep].view(np.int64)), f"{where}: special z0 changed"
     assert np.array_equal(z1[keep].view(np.int64), w1[keep].view(np.int64)), f"{where}: special z1 changed"
     # and z0 is the correctly rounded f(x0 + x1) wherever the twofold's own error
-    # bound (2^-100 |F| + 2^-52 |F - f(x0)| + 2^-1074: z1 carries the x1 term to 1x)
-    # cannot reach a rounding midpoint; within one ulp everywhere
+    # bound (2^-100 |F| + 2^-53 |F - f(x0)| + 2^-1074: z1 holds the deviation to
+    # half its ulp plus 2^-100 |F|) cannot reach a rounding midpoint; within one
+    # ulp everywhere
     twofold = oracle.evaluate(base, x0, x1)
     orc = oracle.coupled(twofold)
     rel_tol, ulp_tol, abs_tol = tfcheck.TOL["f64"]
