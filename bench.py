@@ -9,14 +9,23 @@ flush is needed between iterations.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  ``value`` is elements processed per second by
-all ranks (Gelem/s); ``e2e`` is the same metric through the host-array API
-(pinned host -> device -> host, copies inside the timed region); ``roofline``
-is for the kernel with the longest average launch; ``cpu_baseline`` is the
-CPU oracle timed on this host's cores on a bounded sample.
+Prints one JSON line (rank 0).  ``value`` is the metric, texp/tlog Gelem/s at
+n = 2^26: 2n elements (n of texp, n of tlog) per rank over the two kernels'
+time, CUDA events on the launching stream inside the timed step, summed over
+ranks; the whole six-function step is reported under ``step``.  ``e2e`` is the
+same metric through the host-array API (the kernels read and write pinned host
+memory, so every byte crosses the host link inside the timed region);
+``roofline`` is for the metric's dominant kernel; ``cpu_baseline`` is the CPU
+oracle timed on this host's cores on a bounded sample of texp and tlog.
 
 ``--impl reference`` times the CPU oracle (binary128, all host cores) as the
 reference arm on bounded samples of the same workload.
+
+``--ncu-summary CSV`` prints the per-kernel count table (markdown) of an ncu
+``--csv`` metric capture of this benchmark, stamped with the hash of the
+kernel sources; the benchmark reads its instruction counts and DRAM traffic
+from that table (profiles/pipe_counts_unary_v2_binary_v2_n2p24.md) and drops
+the traffic when the sources have changed since.
 """
 from __future__ import annotations
 
@@ -33,41 +42,124 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FUNCS = ("texp", "texpm1", "tlog", "tlog1p", "tadd", "tmul")
+METRIC_FUNCS = ("texp", "tlog")
 METRIC = "double-twofold texp/tlog Gelem/s at n=2^26 and % of FP64/HBM roofline"
 WORKLOAD = ("texp, texpm1, tlog, tlog1p (+ tadd, tmul) over double twofolds, n=2^26 each: exp/expm1 "
             "args random sign |x0| log-uniform in [2^-40, 708]; log x0 log-uniform in [2^-1020, 2^1020]; "
             "log1p half |x0| log-uniform in [2^-40, 2^-10), half -1+2^-30 .. 2^100; x1 = x0*u*2^-53")
 
-# Per-element instruction counts of each kernel on its workload, from one ncu
-# --set full capture per kernel at n = 2^25 (profiles/unary_v2_intcore_n2p25.md,
-# profiles/binary_v2_tadd_tmul_n2p25.md):
-# * FP64-pipe thread instructions: smsp__sass_thread_inst_executed_op_{dadd,dmul,
-#   dfma}_pred_on (the dadd class includes FP64 compares) x cycles / n; it equals
-#   sm__inst_executed_pipe_fp64 utilisation x 2 per SM per cycle x cycles / n;
-# * integer-ALU-pipe thread instructions: sm__inst_executed_pipe_alu utilisation
-#   x 64 per SM per cycle x active cycles / n (16 lanes per SM sub-partition: the
-#   same derivation with the issue rate reproduces smsp__inst_executed exactly).
-FP64_PER_ELEM = {"texp": 9.0, "texpm1": 10.0, "tlog": 11.0, "tlog1p": 18.0, "tadd": 5.0, "tmul": 4.0}
-ALU_PER_ELEM = {"texp": 295.0, "texpm1": 385.0, "tlog": 496.0, "tlog1p": 587.0, "tadd": 33.0, "tmul": 25.0}
-COUNT_SOURCE = "ncu pipe counters, one --set full capture per kernel at n=2^25"
-ALU_LANES_PER_SM_CLK = 64
+# Per-element instruction counts and DRAM traffic of each kernel on its
+# workload come from one ncu metric capture of this benchmark, summarised in
+# COUNTS_FILE (written by --ncu-summary): integer-ALU-pipe, FP64-pipe and
+# FMA-pipe thread instructions per element (warp instructions x 32 / n; every
+# warp of these kernels runs all 32 lanes) and dram__bytes_read + write per
+# launch.  The file carries the hash of the kernel sources it was taken on.
+COUNTS_FILE = os.path.join(ROOT, "profiles", "pipe_counts_unary_v2_binary_v2_n2p24.md")
+KERNEL_SOURCES = ("tf_capi.cu", "tf_core.cuh", "tf_core_f.cuh", "tf_fixed.cuh", "tf_eft.cuh", "tf_tables.h")
+NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,sm__inst_executed_pipe_alu.sum,"
+               "sm__inst_executed_pipe_fp64.sum,sm__inst_executed_pipe_fma.sum,smsp__inst_executed.sum,"
+               "sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active,"
+               "sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active")
 # HBM bytes per element: SoA doubles in + out.
 BYTES_PER_ELEM = {"texp": 32, "texpm1": 32, "tlog": 32, "tlog1p": 32, "tadd": 48, "tmul": 48}
-HBM_PEAK_GBS = 6804.4   # MEASURED_PEAKS.json hbm_gbs (STREAM-style copy on the GB300s)
-SM_MAX_MHZ = 2070.0     # MEASURED_PEAKS.json sm_max_mhz (used when no clock sample exists)
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# same captures at n = 2^25, scaled by 2 to the benchmark's n = 2^26 (the traffic
-# of an elementwise kernel is proportional to n).  The writes still held in L2 when
-# a launch ends are not in its count.
-TRAFFIC_PER_LAUNCH = {"texp": 2.0510e9, "texpm1": 2.0520e9, "tlog": 2.0470e9, "tlog1p": 2.0472e9,
-                      "tadd": 3.1480e9, "tmul": 3.1481e9}
-TRAFFIC_N = 1 << 26
-# Pipe utilisation of the same captures (% of peak while active): the unary
-# kernels are bound by the integer ALU pipe with the FP64 pipe close behind,
-# tadd by the FP64 pipe, tmul by the FP64 pipe and HBM together.
-PIPES = {"texp": {"alu_pct": 71.1, "fp64_pct": 69.5}, "texpm1": {"alu_pct": 74.1, "fp64_pct": 67.8},
-         "tlog": {"alu_pct": 77.5, "fp64_pct": 55.1}, "tlog1p": {"alu_pct": 78.8, "fp64_pct": 77.4},
-         "tadd": {"alu_pct": 17.4, "fp64_pct": 83.1}, "tmul": {"alu_pct": 18.6, "fp64_pct": 93.4}}
+HBM_PEAK_FALLBACK = 6804.4   # GB/s, a measured copy on the GB300s, when MEASURED_PEAKS.json is absent
+SM_MAX_MHZ = 2070.0          # used when no clock sample exists
+
+
+def hbm_peak():
+    """(GB/s, source) of the HBM roof: MEASURED_PEAKS.json's measured copy
+    bandwidth when the file is present, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured: MEASURED_PEAKS.json hbm_gbs (STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return HBM_PEAK_FALLBACK, "fallback: an earlier measured copy on a GB300"
+
+
+def kernel_source_hash() -> str:
+    """Hash of the elementwise kernels' sources with comments and blank space
+    removed (a comment edit does not stale the counts; a code edit does)."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1502_05216_gb300", "csrc")
+    for name in KERNEL_SOURCES:
+        text = open(os.path.join(csrc, name)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(name.encode())
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()[:16]
+
+
+def load_counts(path: str = COUNTS_FILE):
+    """{kernel: {alu, fp64, fma, inst, traffic, n}} and the source hash from the
+    count table; ({}, None) when the file is missing."""
+    out, stamp = {}, None
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return out, stamp
+    for ln in lines:
+        if ln.startswith("kernel source hash:"):
+            stamp = ln.split(":", 1)[1].strip().strip("`")
+        c = [x.strip() for x in ln.strip().strip("|").split("|")]
+        if len(c) == 9 and c[0] in FUNCS + tuple(f + "f" for f in FUNCS[:4]):
+            try:
+                out[c[0]] = {"n": int(c[1]), "alu": float(c[3]), "fp64": float(c[4]), "fma": float(c[5]),
+                             "inst": float(c[6]), "traffic_per_elem": float(c[7])}
+            except ValueError:
+                continue
+    return out, stamp
+
+
+def ncu_summary(csv_path: str) -> str:
+    """Markdown count table from an ncu --csv metric capture of this benchmark:
+    the first captured launch of each kernel, in launch order."""
+    import csv
+    import re
+    rows, order = {}, []
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    names = {"OpExp": "texp", "OpExpm1": "texpm1", "OpLog": "tlog", "OpLog1p": "tlog1p", "OpAdd": "tadd",
+             "OpMul": "tmul", "OpExpF": "texpf", "OpExpm1F": "texpm1f", "OpLogF": "tlogf", "OpLog1pF": "tlog1pf"}
+    first = {}
+    for r in csv.DictReader(lines):
+        op = re.search(r"\b(Op[A-Za-z0-9]+)\b", r["Kernel Name"])
+        nm = names.get(op.group(1) if op else "")
+        if nm is None:
+            continue
+        if nm not in first:
+            first[nm] = r["ID"]
+            order.append(nm)
+            rows[nm] = {}
+        if r["ID"] != first[nm]:
+            continue
+        v = r["Metric Value"].replace(",", "")
+        rows[nm][r["Metric Name"]] = (float(v), r["Metric Unit"])
+    n = N_FOR_SUMMARY[0]
+    out = [f"kernel source hash: `{kernel_source_hash()}`", "",
+           "| kernel | n | ms (serialised) | ALU inst/elem | FP64 inst/elem | FMA inst/elem | all inst/elem | "
+           "DRAM bytes/elem | ALU %, FP64 % of peak (active) |", "|---|---|---|---|---|---|---|---|---|"]
+    scale = {"nsecond": 1e-6, "ns": 1e-6, "usecond": 1e-3, "us": 1e-3, "msecond": 1.0, "ms": 1.0,
+             "byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    for nm in order:
+        m = rows[nm]
+        val = lambda k: m[k][0] * scale.get(m[k][1], 1.0)  # noqa: E731
+        per = lambda k: m[k][0] * 32 / n  # noqa: E731
+        byts = val("dram__bytes_read.sum") + val("dram__bytes_write.sum")
+        out.append(f"| {nm} | {n} | {val('gpu__time_duration.sum'):.4f} | {per('sm__inst_executed_pipe_alu.sum'):.1f} | "
+                   f"{per('sm__inst_executed_pipe_fp64.sum'):.1f} | {per('sm__inst_executed_pipe_fma.sum'):.1f} | "
+                   f"{per('smsp__inst_executed.sum'):.1f} | {byts / n:.2f} | "
+                   f"{m['sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active'][0]:.1f}, "
+                   f"{m['sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active'][0]:.1f} |")
+    return "\n".join(out)
+
+
+N_FOR_SUMMARY = [1 << 24]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -83,9 +175,13 @@ def parse():
     ap.add_argument("--no-coupled", action="store_true",
                     help="skip the variant entry points (pexp ... tlog1pp, texp_tables)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the size sweep")
+    ap.add_argument("--no-hard", action="store_true", help="skip the timed hard-case sets")
     ap.add_argument("--tier-log2n", type=int, default=28)
-    ap.add_argument("--sweep-max", type=int, default=26, choices=(26, 28, 30),
-                    help="largest size of the sweep (2^28 and 2^30 draw their own inputs: 4 / 16 GiB per array)")
+    ap.add_argument("--sweep-max", type=int, default=30, choices=(26, 28, 30),
+                    help="largest size of the sweep (2^28 and 2^30 draw their own inputs: 2 / 8 GiB per array)")
+    ap.add_argument("--ncu-summary", default=None, metavar="CSV",
+                    help="print the count table of an ncu --csv capture of this benchmark and exit")
+    ap.add_argument("--ncu-n", type=int, default=1 << 24, help="n of the captured launches (--ncu-summary)")
     ap.add_argument("--funcs", default=",".join(FUNCS),
                     help="comma-separated subset (for profiling a single kernel)")
     return ap.parse_args()
@@ -166,44 +262,45 @@ class Clocks:
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------------
 
-def oracle_rate(budget_s: float, per_func_cap: int = 1 << 22):
-    """Time the CPU oracle on a bounded sample of every function's workload:
-    elements/s over all host threads, plus the sample description."""
+def oracle_rate(budget_s: float, per_func_cap: int = 1 << 22, funcs=METRIC_FUNCS):
+    """Time the CPU oracle on a bounded sample of the metric's functions'
+    workloads (texp and tlog): elements/s over all host threads, plus the
+    sample description."""
     import oracle
     from paper_1502_05216_gb300 import inputs as I
     lib = oracle.load()
     probe = 1 << 13
     t0 = time.perf_counter()
-    for f in FUNCS:
+    for f in funcs:
         oracle.evaluate(f, *I.workload(f, probe), lib=lib)
-    rate0 = len(FUNCS) * probe / (time.perf_counter() - t0)
-    m = int(min(per_func_cap, max(probe, budget_s * rate0 / len(FUNCS))))
-    args = {f: I.workload(f, m, start=1 << 30) for f in FUNCS}
+    rate0 = len(funcs) * probe / (time.perf_counter() - t0)
+    m = int(min(per_func_cap, max(probe, budget_s * rate0 / len(funcs))))
+    args = {f: I.workload(f, m, start=1 << 30) for f in funcs}
     t0 = time.perf_counter()
-    for f in FUNCS:
+    for f in funcs:
         oracle.evaluate(f, *args[f], lib=lib)
     dt = time.perf_counter() - t0
-    sample = f"{m} elements of each of the 6 functions' workloads (indices from 2^30), {dt:.1f} s"
-    return len(FUNCS) * m / dt, oracle.threads(), sample, m, dt
+    sample = f"{m} elements of each of {', '.join(funcs)}'s workloads (indices from 2^30), {dt:.1f} s"
+    return len(funcs) * m / dt, oracle.threads(), sample, m, dt
 
 
-def oracle_single_core(m: int):
+def oracle_single_core(m: int, funcs=METRIC_FUNCS):
     """The oracle on one host thread: m elements of each function's workload."""
     import oracle
     from paper_1502_05216_gb300 import inputs as I
     lib = oracle.load()
     t = oracle.threads()
-    args = {f: I.workload(f, m, start=1 << 32) for f in FUNCS}
+    args = {f: I.workload(f, m, start=1 << 32) for f in funcs}
     oracle.set_threads(1)
     try:
         t0 = time.perf_counter()
-        for f in FUNCS:
+        for f in funcs:
             oracle.evaluate(f, *args[f], lib=lib)
         dt = time.perf_counter() - t0
     finally:
         oracle.set_threads(t)
-    return {"value": len(FUNCS) * m / dt / 1e9, "unit": "Gelem/s", "cores": 1,
-            "sample": f"{m} elements of each of the 6 functions' workloads (indices from 2^32), {dt:.1f} s"}
+    return {"value": len(funcs) * m / dt / 1e9, "unit": "Gelem/s", "cores": 1,
+            "sample": f"{m} elements of each of {', '.join(funcs)}'s workloads (indices from 2^32), {dt:.1f} s"}
 
 
 def reference_arm(a, world, rank):
@@ -214,22 +311,22 @@ def reference_arm(a, world, rank):
     lib = oracle.load()
     budget = max(1.0, min(8.0, 150.0 / (a.steps + a.warmup)))
     _, cores, _, m, _ = oracle_rate(budget * 0.5)
-    args = {f: I.workload(f, m, start=1 << 31) for f in FUNCS}
+    args = {f: I.workload(f, m, start=1 << 31) for f in METRIC_FUNCS}
     for _ in range(a.warmup):
-        for f in FUNCS:
+        for f in METRIC_FUNCS:
             oracle.evaluate(f, *args[f], lib=lib)
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        for f in FUNCS:
+        for f in METRIC_FUNCS:
             oracle.evaluate(f, *args[f], lib=lib)
     dt = (time.perf_counter() - t0) / a.steps
-    v = len(FUNCS) * m / dt / 1e9
-    sample = f"each step: {m} elements of each of the 6 functions' workloads (bounded sample of n=2^26)"
+    v = len(METRIC_FUNCS) * m / dt / 1e9
+    sample = f"each step: {m} elements of each of texp's and tlog's workloads (bounded sample of n=2^26)"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "Gelem/s", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f128", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": 1 << a.log2n, "functions": list(FUNCS)},
+        "config": {"workload": WORKLOAD, "n": 1 << a.log2n, "functions": list(METRIC_FUNCS)},
         "cpu_baseline": {"value": v, "unit": "Gelem/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -263,6 +360,34 @@ def fp64_peak(dev):
         if i >= 2:
             best = max(best, blocks * threads * iters * 8 / (e0.elapsed_time(e1) * 1e-3))
     return best, sms
+
+
+def alu_peak(dev, mode=0):
+    """Measured integer-ALU pipe rate (thread-instructions/s) of this GPU, from
+    the calibration kernel (16 instructions per iteration and thread; mode 0:
+    rotates and three-input xors, which only the ALU pipe executes); best of 5."""
+    import ctypes
+    import torch
+    from paper_1502_05216_gb300 import build
+    lib = ctypes.CDLL(build.PROBE_LIB)
+    lib.tfp_alu.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_void_p]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads, iters = sms * 8, 256, 20000
+    out = torch.empty(blocks * threads, dtype=torch.int32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    best = 0.0
+    for i in range(7):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        rc = lib.tfp_alu(out.data_ptr(), blocks, threads, iters, mode, st.cuda_stream)
+        e1.record(st)
+        e1.synchronize()
+        if rc != 0:
+            raise RuntimeError(f"tfp_alu failed ({rc})")
+        if i >= 2:
+            best = max(best, blocks * threads * iters * 16 / (e0.elapsed_time(e1) * 1e-3))
+    return best
 
 
 CHAIN_WORKLOAD = ("65,536 independent chains, lengths geometric (mean 256, cap 4096), ops uniform over "
@@ -322,14 +447,17 @@ def chains_bench(dev, rank=0, world=1):
     fused = reduce_max(cb.time_graph(cb.graph("fused", cfg["threads"], cfg["blocks"], cfg["group"]), 5), world, dev)
     per_op = reduce_max(cb.time_graph(cb.graph("per_op"), 5), world, dev)
     ops = int(full["step_base"][-1])
+    best = sorted(table, key=lambda r: r["ms"])
+    # the headline figures last, so that the end of the JSON line carries them
     return {"workload": CHAIN_WORKLOAD, "ops": ops, "mix": dict(zip(("tadd", "tmul", "texp", "tlog"),
                                                                     full["mix"].tolist())),
-            "max_len": int(full["max_len"]), "fused_ms": fused, "per_op_ms": per_op, "speedup": per_op / fused,
-            "fused_gops_s": ops / (fused * 1e-3) / 1e9, "fused_config": cfg,
-            "per_op_launches": cb.per_op_launches, "ranks": world,
+            "max_len": int(full["max_len"]), "per_op_launches": cb.per_op_launches, "ranks": world,
             "scaling": "strong (chains sharded by chain id)" if world > 1 else None,
-            "tuning_cols": ["group", "threads", "blocks", "ms"],
-            "tuning": [[r["group"], r["threads"], r["blocks"], round(r["ms"], 3)] for r in table]}
+            "tuning": {"tried": len(table), "cols": ["group", "threads", "blocks", "ms"],
+                       "fastest": [[r["group"], r["threads"], r["blocks"], round(r["ms"], 3)] for r in best[:4]],
+                       "slowest_ms": round(best[-1]["ms"], 3)},
+            "fused_config": cfg, "fused_gops_s": ops / (fused * 1e-3) / 1e9,
+            "fused_ms": fused, "per_op_ms": per_op, "speedup": per_op / fused}
 
 
 def _time_launches(fn, reps=5, warm=3):
@@ -412,7 +540,7 @@ def precision_tier(dev, log2n):
             o = (torch.empty_like(d0), torch.empty_like(d0))
             ms = _time_launches(lambda: fn(d0, d1, out=o))
             res[dt] = {"ms": ms, "gelem_s": n / (ms * 1e-3) / 1e9, "hbm_gbs": bpe * n / (ms * 1e-3) / 1e9,
-                       "hbm_frac": bpe * n / (ms * 1e-3) / 1e9 / HBM_PEAK_GBS}
+                       "hbm_frac": bpe * n / (ms * 1e-3) / 1e9 / hbm_peak()[0]}
             del d0, d1, o
         res["f32_over_f64"] = res["f64"]["ms"] / res["f32"]["ms"]
         out[func] = res
@@ -464,6 +592,30 @@ def size_sweep(dev, dargs, max_lg=26):
     return out
 
 
+def hard_case_timing(dev, dargs, log2n=24):
+    """texp and tlog (double) over the 2^24 hard-case set of the parity tests
+    (thresholds of overflow, underflow and subnormal results, tiny and huge
+    arguments, log near 1, subnormal y0, x1 = 0, half-ulp x1, IEEE specials)
+    against the first 2^24 elements of their workloads: the cost of the lanes
+    that leave the straight-line code (each warp votes once and runs its rare
+    lanes' branch).  CUDA events, median of 5 launches."""
+    import torch
+    from paper_1502_05216_gb300 import inputs as I, tf
+    n = 1 << log2n
+    out = {"n": n}
+    for func in METRIC_FUNCS:
+        h = [torch.from_numpy(x).to(dev) for x in I.hard_cases(func, n, seed=29)]
+        w = [x[:n] for x in dargs[func]]
+        o = (torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.float64, device=dev))
+        ms_h = _time_launches(lambda: tf.FUNCS[func](*h, out=o))
+        ms_w = _time_launches(lambda: tf.FUNCS[func](*w, out=o))
+        out[func] = {"hard_ms": ms_h, "workload_ms": ms_w, "hard_gelem_s": n / (ms_h * 1e-3) / 1e9,
+                     "workload_gelem_s": n / (ms_w * 1e-3) / 1e9, "time_ratio": ms_h / ms_w}
+        del h, o
+    torch.cuda.empty_cache()
+    return out
+
+
 def ours(a, world, rank, local):
     global FUNCS
     FUNCS = tuple(f for f in a.funcs.split(",") if f)
@@ -499,6 +651,8 @@ def ours(a, world, rank, local):
                 evs[f][1].record(st)
 
     peak, sms = fp64_peak(dev)
+    alu = alu_peak(dev, 0)
+    alu_imad = alu_peak(dev, 1)
     for _ in range(a.warmup):
         step()
     evs = [{f: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for f in FUNCS}
@@ -521,80 +675,95 @@ def ours(a, world, rank, local):
     ms = t0.elapsed_time(t1) / a.steps
     kern_ms = {f: statistics.mean(e[f][0].elapsed_time(e[f][1]) for e in evs) for f in FUNCS}
     ms = reduce_max(ms, world, dev)
-    elems = world * n * len(FUNCS)
-    value = elems / (ms * 1e-3) / 1e9
+    mfuncs = [f for f in METRIC_FUNCS if f in FUNCS] or list(FUNCS)
+    metric_ms = reduce_max(sum(kern_ms[f] for f in mfuncs), world, dev)
+    value = world * n * len(mfuncs) / (metric_ms * 1e-3) / 1e9
+    step_value = world * n * len(FUNCS) / (ms * 1e-3) / 1e9
 
-    # end to end through the host-array API: pinned host buffers in and out,
-    # every byte crosses the GPU's host link inside the timed region
+    # end to end through the host-array API: the metric's functions on pinned host
+    # buffers, every byte crossing the GPU's host link inside the timed region
     e2e = None
     if not a.no_e2e:
-        pin = {f: [torch.from_numpy(x).pin_memory() for x in host[f]] for f in FUNCS}
+        pin = {f: [torch.from_numpy(x).pin_memory() for x in host[f]] for f in mfuncs}
         outs = {f: (torch.empty(n, dtype=torch.float64, pin_memory=True),
-                    torch.empty(n, dtype=torch.float64, pin_memory=True)) for f in FUNCS}
-        h2d = sum(8 * n * len(host[f]) for f in FUNCS)
-        d2h = 16 * n * len(FUNCS)
-        e2e = {}
+                    torch.empty(n, dtype=torch.float64, pin_memory=True)) for f in mfuncs}
+        h2d = sum(8 * n * len(host[f]) for f in mfuncs)
+        d2h = 16 * n * len(mfuncs)
+        res = {}
         for mode in ("zero-copy", "pipeline"):
-            for f in FUNCS:
+            for f in mfuncs:
                 tf.call_host(f, *pin[f], out=outs[f], device=dev, mode=mode)
-            ke = max(2, a.steps // 4)
+            ke = max(3, a.steps // 2)
             barrier()
             c0 = time.perf_counter()
             for _ in range(ke):
-                for f in FUNCS:
+                for f in mfuncs:
                     tf.call_host(f, *pin[f], out=outs[f], device=dev, mode=mode)
             barrier()
             dt = reduce_max((time.perf_counter() - c0) / ke, world, dev)
-            e2e[mode] = {"value": elems / dt / 1e9, "ms_per_step": dt * 1e3}
+            res[mode] = {"value": world * n * len(mfuncs) / dt / 1e9, "ms_per_step": dt * 1e3}
         link = host_link(dev)
-        moved = (h2d + d2h) / (e2e["zero-copy"]["ms_per_step"] * 1e-3) / 1e9
+        moved = (h2d + d2h) / (res["zero-copy"]["ms_per_step"] * 1e-3) / 1e9
         link.update({"achieved_gbs": moved, "frac": moved / link["both_gbs"],
                      "note": "achieved = (h2d + d2h bytes per step) / zero-copy time per step; frac of both_gbs"})
-        e2e = {"value": e2e["zero-copy"]["value"], "unit": "Gelem/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e2e["zero-copy"]["ms_per_step"], "link": link,
-               "mode": "zero-copy: the kernels load x0/x1 (y0/y1) from pinned host memory and store z0/z1 "
-                       "there, over the host link (tf.call_host default)",
-               "pipeline": {"value": e2e["pipeline"]["value"], "ms_per_step": e2e["pipeline"]["ms_per_step"],
+        e2e = {"value": res["zero-copy"]["value"], "unit": "Gelem/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": res["zero-copy"]["ms_per_step"],
+               "functions": mfuncs, "link": link,
+               "mode": "zero-copy: the kernels load x0/x1 from pinned host memory and store z0/z1 there, "
+                       "over the host link (tf.call_host default)",
+               "pipeline": {"value": res["pipeline"]["value"], "ms_per_step": res["pipeline"]["ms_per_step"],
                             "mode": "chunked H2D copy, kernel, D2H copy over 3 streams (tf.HostPipeline)"}}
+        del pin, outs
 
     # every rank runs its shard of the chains (the times are the slowest rank's)
     chain = None if a.no_chains else chains_bench(dev, rank, world)
     if rank != 0:
         return
-    dom = max(FUNCS, key=lambda f: kern_ms[f])
-    d = kern_ms[dom] * 1e-3
+    hpeak, hsrc = hbm_peak()
+    counts, stamp = load_counts()
+    current = stamp is not None and stamp == kernel_source_hash()
     mhz = ck.get("sm_mhz") or SM_MAX_MHZ
-    alu_peak = ALU_LANES_PER_SM_CLK * sms * mhz * 1e6
-    views = {
-        "integer": {"achieved": ALU_PER_ELEM[dom] * n / d / 1e9, "peak": alu_peak / 1e9,
-                    "unit": "integer-ALU-pipe Ginst/s", "inst_per_elem": ALU_PER_ELEM[dom],
-                    "peak_source": f"derived: {ALU_LANES_PER_SM_CLK} integer-ALU lanes per SM per clock x {sms} SMs x "
-                                   f"{mhz:.0f} MHz ({'median SM clock sampled in the timed region' if ck.get('sm_mhz') else 'SM max clock'})"},
-        "fp64": {"achieved": FP64_PER_ELEM[dom] * n / d / 1e9, "peak": peak / 1e9, "unit": "FP64 Ginst/s",
-                 "inst_per_elem": FP64_PER_ELEM[dom],
-                 "peak_source": f"measured: DFMA calibration kernel on this GPU ({sms} SMs)"},
-    }
-    for v in views.values():
-        v["frac"] = v["achieved"] / v["peak"]
-    pipe = max(views, key=lambda k: views[k]["frac"])
-    other = "fp64" if pipe == "integer" else "integer"
-    roof = {"bound": "alu", "pipe": pipe, "kernel": dom, **views[pipe], "count_source": COUNT_SOURCE,
-            "traffic": TRAFFIC_PER_LAUNCH.get(dom) if n == TRAFFIC_N else None,
-            "traffic_source": "ncu dram bytes of one launch at n=2^25, x2" if n == TRAFFIC_N else None,
-            "ncu_pipes_pct": PIPES.get(dom), f"{other}_view": views[other],
-            "hbm_view": {"achieved_gbs": BYTES_PER_ELEM[dom] * n / d / 1e9, "peak_gbs": HBM_PEAK_GBS,
-                         "frac": BYTES_PER_ELEM[dom] * n / d / 1e9 / HBM_PEAK_GBS,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}
+    dom = max(mfuncs, key=lambda f: kern_ms[f])
+    d = kern_ms[dom] * 1e-3
+    cnt = counts.get(dom, {})
+    count_src = (f"ncu metric capture, {os.path.relpath(COUNTS_FILE, ROOT)} (kernel source hash {stamp}: "
+                 f"{'current' if current else 'STALE: the kernels changed since the capture'})")
+    views = {}
+    if cnt:
+        views["integer"] = {"achieved": cnt["alu"] * n / d / 1e9, "peak": alu / 1e9, "unit": "integer-ALU-pipe Ginst/s",
+                            "inst_per_elem": cnt["alu"],
+                            "peak_source": f"measured: integer-ALU calibration kernel on this GPU ({sms} SMs)"}
+        views["fp64"] = {"achieved": cnt["fp64"] * n / d / 1e9, "peak": peak / 1e9, "unit": "FP64 Ginst/s",
+                         "inst_per_elem": cnt["fp64"],
+                         "peak_source": f"measured: DFMA calibration kernel on this GPU ({sms} SMs)"}
+        for v in views.values():
+            v["frac"] = v["achieved"] / v["peak"]
+    hbm = {"achieved": BYTES_PER_ELEM[dom] * n / d / 1e9, "peak": hpeak, "unit": "GB/s",
+           "frac": BYTES_PER_ELEM[dom] * n / d / 1e9 / hpeak, "peak_source": hsrc}
+    traffic = cnt["traffic_per_elem"] * n if (cnt and current) else None
+    if views:
+        pipe = max(views, key=lambda k: views[k]["frac"])
+        other = "fp64" if pipe == "integer" else "integer"
+        roof = {"bound": "alu", "pipe": pipe, "kernel": dom, **views[pipe], "traffic": traffic,
+                "traffic_unit": "bytes per launch (dram read + write)", "count_source": count_src,
+                "counts_current": current, f"{other}_view": views[other], "hbm_view": hbm,
+                "alu_peak_note": f"{alu / (sms * mhz * 1e6):.1f} ALU thread-instructions per SM per clock at the "
+                                 f"sampled {mhz:.0f} MHz"}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, **hbm, "traffic": None, "count_source": "no count table"}
     per = {}
     for f in FUNCS:
         t = kern_ms[f] * 1e-3
-        fr = {"alu": ALU_PER_ELEM[f] * n / t / alu_peak, "fp64": FP64_PER_ELEM[f] * n / t / peak,
-              "hbm": BYTES_PER_ELEM[f] * n / t / 1e9 / HBM_PEAK_GBS}
+        c = counts.get(f)
+        fr = {"hbm": BYTES_PER_ELEM[f] * n / t / 1e9 / hpeak}
+        if c:
+            fr["alu"] = c["alu"] * n / t / alu
+            fr["fp64"] = c["fp64"] * n / t / peak
         b = max(fr, key=fr.get)
         per[f] = {"ms": kern_ms[f], "gelem_s": n / t / 1e9, "hbm_gbs": BYTES_PER_ELEM[f] * n / t / 1e9,
-                  "alu_frac": fr["alu"], "fp64_frac": fr["fp64"], "hbm_frac": fr["hbm"],
-                  "binding": b, "binding_frac": fr[b]}
-    sweep = None if (a.no_sweep or a.log2n < 26 or "texp" not in dargs or "tlog" not in dargs) else size_sweep(dev, dargs, a.sweep_max)
+                  **{k + "_frac": v for k, v in fr.items()}, "binding": b, "binding_frac": fr[b]}
+    hard = None if (a.no_hard or a.log2n < 24 or not set(METRIC_FUNCS) <= set(dargs)) else hard_case_timing(dev, dargs)
+    sweep = None if (a.no_sweep or a.log2n < 26 or not set(METRIC_FUNCS) <= set(dargs)) else size_sweep(dev, dargs, a.sweep_max)
     tier = None if a.no_tier else precision_tier(dev, a.tier_log2n)
     coupled = (None if a.no_coupled or not {"texp", "texpm1", "tlog", "tlog1p"} <= set(dargs)
                else coupled_variants(dev, dargs, n))
@@ -607,16 +776,28 @@ def ours(a, world, rank, local):
         "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "functions": list(FUNCS),
+        "config": {"workload": WORKLOAD, "n": n, "functions": list(FUNCS), "metric_functions": mfuncs,
+                   "value": "2n / (texp + tlog kernel time), CUDA events on the launching stream inside the "
+                            "timed six-function step, summed over ranks",
                    "l2": "no flush: every input array (512 MiB) is larger than L2", "parallelism": f"dp{world}"},
+        "metric_ms": metric_ms,
+        "step": {"functions": list(FUNCS), "ms": ms, "gelem_s": step_value},
+        "peaks": {"alu_ginst_s": alu / 1e9, "alu_per_sm_clk": alu / (sms * mhz * 1e6),
+                  "alu_plus_imad_ginst_s": alu_imad / 1e9, "fp64_ginst_s": peak / 1e9,
+                  "fp64_per_sm_clk": peak / (sms * mhz * 1e6), "hbm_gbs": hpeak, "sm_mhz": mhz,
+                  "source": "alu, fp64: calibration kernels of libtfprobe.so timed here; hbm: " + hsrc},
         "roofline": roof, "per_func": per, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": len(FUNCS) * a.steps, "clocks": ck, "chains": chain, "precision_tier": tier,
-        "size_sweep": sweep, "variants": coupled,
+        "gpu_launches": len(FUNCS) * a.steps, "clocks": ck, "hard_cases": hard, "precision_tier": tier,
+        "size_sweep": sweep, "variants": coupled, "chains": chain,
     }), flush=True)
 
 
 def main():
     a = parse()
+    if a.ncu_summary:
+        N_FOR_SUMMARY[0] = a.ncu_n
+        print(ncu_summary(a.ncu_summary))
+        return
     world, rank, local = dist()
     if world != a.gpus and not (world == 1 and a.gpus == 1):
         if rank == 0:
