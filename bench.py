@@ -106,6 +106,12 @@ def load_counts(path: str = COUNTS_FILE):
         if ln.startswith("kernel source hash:"):
             stamp = ln.split(":", 1)[1].strip().strip("`")
         c = [x.strip() for x in ln.strip().strip("|").split("|")]
+        if len(c) == 4 and c[0] in FUNCS and c[0] in out:  # the full-size traffic table
+            try:
+                out[c[0]]["traffic_n"] = int(c[1])
+                out[c[0]]["traffic"] = float(c[2])
+            except ValueError:
+                pass
         if len(c) == 9 and c[0] in FUNCS + tuple(f + "f" for f in FUNCS[:4]):
             try:
                 out[c[0]] = {"n": int(c[1]), "alu": float(c[3]), "fp64": float(c[4]), "fma": float(c[5]),
@@ -140,6 +146,17 @@ def ncu_summary(csv_path: str) -> str:
         v = r["Metric Value"].replace(",", "")
         rows[nm][r["Metric Name"]] = (float(v), r["Metric Unit"])
     n = N_FOR_SUMMARY[0]
+    if order and "sm__inst_executed_pipe_alu.sum" not in rows[order[0]]:
+        # a DRAM-traffic capture alone (the full-size launches, one pass)
+        out = ["| kernel | n | DRAM bytes per launch (read + write) | ms (serialised) |", "|---|---|---|---|"]
+        for nm in order:
+            m = rows[nm]
+            b = sum(m[k][0] * {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(m[k][1], 1.0)
+                    for k in ("dram__bytes_read.sum", "dram__bytes_write.sum"))
+            t = m["gpu__time_duration.sum"]
+            ms = t[0] * {"nsecond": 1e-6, "ns": 1e-6, "usecond": 1e-3, "us": 1e-3, "msecond": 1.0}.get(t[1], 1.0)
+            out.append(f"| {nm} | {n} | {b:.0f} | {ms:.4f} |")
+        return "\n".join(out)
     out = [f"kernel source hash: `{kernel_source_hash()}`", "",
            "| kernel | n | ms (serialised) | ALU inst/elem | FP64 inst/elem | FMA inst/elem | all inst/elem | "
            "DRAM bytes/elem | ALU %, FP64 % of peak (active) |", "|---|---|---|---|---|---|---|---|---|"]
@@ -740,7 +757,13 @@ def ours(a, world, rank, local):
             v["frac"] = v["achieved"] / v["peak"]
     hbm = {"achieved": BYTES_PER_ELEM[dom] * n / d / 1e9, "peak": hpeak, "unit": "GB/s",
            "frac": BYTES_PER_ELEM[dom] * n / d / 1e9 / hpeak, "peak_source": hsrc}
-    traffic = cnt["traffic_per_elem"] * n if (cnt and current) else None
+    # DRAM bytes per launch: the full-size capture when its n is the benchmark's,
+    # else the small capture scaled by n (an underestimate: part of a small
+    # launch's output is still in L2 when it ends)
+    if cnt and current:
+        traffic = cnt["traffic"] if cnt.get("traffic_n") == n else cnt["traffic_per_elem"] * n
+    else:
+        traffic = None
     if views:
         pipe = max(views, key=lambda k: views[k]["frac"])
         other = "fp64" if pipe == "integer" else "integer"
