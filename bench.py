@@ -521,20 +521,24 @@ def coupled_variants(dev, dargs, n, reps=5):
             res[key] = e0.elapsed_time(e1) / reps
         out[name] = {"ms": res[name], "gelem_s": n / (res[name] * 1e-3) / 1e9, "twofold": base,
                      "twofold_ms": res[base], "time_ratio": res[name] / res[base]}
-    # A/B: texp through the paper's own table reduction (same inputs)
-    res = {}
-    for key, f in (("texp_tables", tf.texp_tables), ("texp", tf.texp)):
-        f(*dargs["texp"], out=(z0, z1), stream=st)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(reps):
-            f(*dargs["texp"], out=(z0, z1), stream=st)
-        e1.record(st)
-        e1.synchronize()
-        res[key] = e0.elapsed_time(e1) / reps
-    out["texp_tables"] = {"ms": res["texp_tables"], "gelem_s": n / (res["texp_tables"] * 1e-3) / 1e9,
-                          "twofold": "texp", "twofold_ms": res["texp"], "time_ratio": res["texp_tables"] / res["texp"],
-                          "what": "the paper's own reduction x = 2m + n/256 + y (K = 8, L = 1), tables e^(2m), e^(n/256)"}
+    # A/B variants: texp through the paper's own table reduction, the logs with
+    # their Newton step in binary64 (same inputs as the default kernels)
+    what = {"texp_tables": "the paper's own reduction x = 2m + n/256 + y (K = 8, L = 1), tables e^(2m), e^(n/256)",
+            "tlog_newton_fp64": "tlog with the Newton step u = t + S + tS in binary64 (S = e^-R - 1 as a pair)",
+            "tlog1p_newton_fp64": "tlog1p with the Newton step u = t + S + tS in binary64"}
+    for var, (fv, base) in tf.VARIANT_FUNCS.items():
+        res = {}
+        for key, f in ((var, fv), (base, tf.FUNCS[base])):
+            f(*dargs[base], out=(z0, z1), stream=st)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                f(*dargs[base], out=(z0, z1), stream=st)
+            e1.record(st)
+            e1.synchronize()
+            res[key] = e0.elapsed_time(e1) / reps
+        out[var] = {"ms": res[var], "gelem_s": n / (res[var] * 1e-3) / 1e9, "twofold": base,
+                    "twofold_ms": res[base], "time_ratio": res[var] / res[base], "what": what[var]}
     return out
 
 

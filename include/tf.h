@@ -124,6 +124,18 @@ int tf_tlog1pp(const double* y0, const double* y1, double* z0, double* z1, int64
  * tf_texp's in its last bits). */
 int tf_texp_tables(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream);
 
+/* tf_tlog and tf_tlog1p with the Newton step taken in binary64 (A/B variants).
+ * Paper: "Twofold logarithm" > "Newton inversion": after the 1x seed R of
+ * log1p(t), one Newton step on e^x gives u = (1 + t) e^-R - 1 and log1p(t) = R +
+ * log1p(u).  tf_tlog/tf_tlog1p take u in exact 128-bit integer fixed point;
+ * these take e^-R - 1 = S and t as pairs of doubles and u = t + S + t S with
+ * binary64 operations (FMA-based exact product, exact sums where the terms
+ * cancel), the paper's own arithmetic for that step.  Same results contract as
+ * tf_tlog/tf_tlog1p (z0 = RN(log y0) resp. RN(log1p y0), z0 + z1 within the
+ * same bound; z1 may differ in its last bits). */
+int tf_tlog_newton_fp64(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
+int tf_tlog1p_newton_fp64(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream);
+
 /* Float twofolds: the same four functions over pairs of floats, with the
  * paper's "f"-suffixed float variants in mind ("Twofold exponent" and
  * "Twofold logarithm" give each algorithm for float and double).  Every

@@ -100,6 +100,18 @@ struct OpExpTables {
     static constexpr int min_blocks = 4;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp_impl<true, true, true>(a, b, z0, z1); }
 };
+// The logarithms with the Newton step in binary64 (A/B variants of OpLog, OpLog1p).
+struct OpLogN64 {
+    static constexpr int min_blocks = 4;
+    static constexpr double dummy = 1.0;
+    __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog_impl<true, true, true>(a, b, z0, z1); }
+};
+struct OpLog1pN64 {
+    static constexpr int threads = 128;
+    static constexpr int min_blocks = 7;
+    static constexpr double dummy = 0.0;
+    __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1p_impl<true, true>(a, b, z0, z1); }
+};
 struct OpAdd {
     __device__ static void eval(double a, double b, double c, double d, double& z0, double& z1) {
         tf::tadd1(a, b, c, d, z0, z1);
@@ -400,6 +412,12 @@ int tf_tlog1pp(const double* y0, const double* y1, double* z0, double* z1, int64
 }
 int tf_texp_tables(const double* x0, const double* x1, double* z0, double* z1, int64_t n, void* stream) {
     return run_unary<OpExpTables>(x0, x1, z0, z1, n, stream);
+}
+int tf_tlog_newton_fp64(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpLogN64>(y0, y1, z0, z1, n, stream);
+}
+int tf_tlog1p_newton_fp64(const double* y0, const double* y1, double* z0, double* z1, int64_t n, void* stream) {
+    return run_unary<OpLog1pN64>(y0, y1, z0, z1, n, stream);
 }
 int tf_tadd(const double* x0, const double* x1, const double* y0, const double* y1, double* z0, double* z1,
             int64_t n, void* stream) {

@@ -21,7 +21,7 @@ BINARY = ("tadd", "tmul")
 # Coupled results (p...) and twofold results of coupled arguments (t...p).
 COUPLED = ("pexp", "pexpm1", "plog", "plog1p", "texpp", "texpm1p", "tlogp", "tlog1pp")
 # the same function computed another way (the paper's own exp reduction)
-VARIANTS = ("texp_tables",)
+VARIANTS = ("texp_tables", "tlog_newton_fp64", "tlog1p_newton_fp64")
 
 
 class TwofoldError(RuntimeError):
@@ -234,6 +234,21 @@ def tlog1pp(y0, y1=None, out=None, stream=None):
 def texp_tables(x0, x1=None, out=None, stream=None):
     """texp computed with the paper's own table reduction (A/B variant)."""
     return _unary("texp_tables", x0, x1, out, stream)
+
+
+def tlog_newton_fp64(y0, y1=None, out=None, stream=None):
+    """tlog with its Newton step in binary64 (A/B variant)."""
+    return _unary("tlog_newton_fp64", y0, y1, out, stream)
+
+
+def tlog1p_newton_fp64(y0, y1=None, out=None, stream=None):
+    """tlog1p with its Newton step in binary64 (A/B variant)."""
+    return _unary("tlog1p_newton_fp64", y0, y1, out, stream)
+
+
+# the A/B variants and the function each computes
+VARIANT_FUNCS = {"texp_tables": (texp_tables, "texp"), "tlog_newton_fp64": (tlog_newton_fp64, "tlog"),
+                 "tlog1p_newton_fp64": (tlog1p_newton_fp64, "tlog1p")}
 
 
 FUNCS_C = {"pexp": pexp, "pexpm1": pexpm1, "plog": plog, "plog1p": plog1p,
