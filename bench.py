@@ -24,7 +24,7 @@ reference arm on bounded samples of the same workload.
 ``--ncu-summary CSV`` prints the per-kernel count table (markdown) of an ncu
 ``--csv`` metric capture of this benchmark, stamped with the hash of the
 kernel sources; the benchmark reads its instruction counts and DRAM traffic
-from that table (profiles/pipe_counts_unary_v2_binary_v2_n2p24.md) and drops
+from that table (profiles/pipe_counts_unary_v2_binary_v2_n2p24.txt) and drops
 the traffic when the sources have changed since.
 """
 from __future__ import annotations
@@ -54,7 +54,7 @@ WORKLOAD = ("texp, texpm1, tlog, tlog1p (+ tadd, tmul) over double twofolds, n=2
 # FMA-pipe thread instructions per element (warp instructions x 32 / n; every
 # warp of these kernels runs all 32 lanes) and dram__bytes_read + write per
 # launch.  The file carries the hash of the kernel sources it was taken on.
-COUNTS_FILE = os.path.join(ROOT, "profiles", "pipe_counts_unary_v2_binary_v2_n2p24.md")
+COUNTS_FILE = os.path.join(ROOT, "profiles", "pipe_counts_unary_v2_binary_v2_n2p24.txt")
 KERNEL_SOURCES = ("tf_capi.cu", "tf_core.cuh", "tf_core_f.cuh", "tf_fixed.cuh", "tf_eft.cuh", "tf_tables.h")
 NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,sm__inst_executed_pipe_alu.sum,"
                "sm__inst_executed_pipe_fp64.sum,sm__inst_executed_pipe_fma.sum,smsp__inst_executed.sum,"
