@@ -19,6 +19,8 @@ Float twofold (float-float on the FP32 pipes) constants:
       with c_i = RN_float(2048 / i): the reciprocal table of the float
       logarithm, log z = -log c_i + log1p(z c_i - 1), |z c_i - 1| < 2^-11.4.
   TF_FT[j], TF_FE[j]  2^(j/512) and 2^(j/512) - 1 as (hi, lo) floats, j = -256 .. 256.
+  TF_FNLN2[n]  n ln2 as (hi, lo) floats (hi = RN_float(n ln2), lo = RN_float of the
+      rest), n = -160 .. 140: the n ln2 term of the float logarithm.
 
 Fixed-point constants of the integer exp core (unsigned integers, rounded to
 nearest, each with its unit):
@@ -158,6 +160,13 @@ def main(out=sys.stdout):
         for zz in (max(z_lo, D("0.70710678")), min(z_hi, D("1.41421357"))):
             assert abs(CTX.subtract(CTX.multiply(zz, D(cf)), 1)) < D(2) ** D("-11.4"), (i, zz)
         w(f"  {{{hexf(cf)}, {hexf(h)}, {hexf(l)}, {hexf(f32_nearest(cm1))}}},\n")
+    w("};\n")
+    w("#define TF_FNLN2_LO (-160)\n")
+    w("/* n ln2 as (hi, lo) floats, n = -160 .. 140; index n + 160 */\n")
+    w("TF_TABLE_QUALIFIER float TF_FNLN2_TABLE[301][2] = {\n")
+    for n in range(-160, 141):
+        h, l = fsplit_exact(CTX.multiply(D(n), ln2), 2)
+        w(f"  {{{hexf(h)}, {hexf(l)}}},\n")
     w("};\n")
     for name, minus1 in (("TF_FT", False), ("TF_FE", True)):
         w(f"/* {'2^(j/512) - 1' if minus1 else '2^(j/512)'} as (hi, lo) floats; index j + 256 */\n")

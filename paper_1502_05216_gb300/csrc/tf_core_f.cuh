@@ -365,7 +365,9 @@ __device__ __forceinline__ void texpm1f_impl(float x0, float x1, float& z0, floa
 //   S = e^-R - 1 = -R + R^2/2 - R^3/6 + R^4/24 - R^5/120 as a float pair,
 //   u = (1 + t)(1 + S) - 1 = t + S + t S   (t + S and t S cancel exactly),
 //   log1p(t) = R + u (u^2/2 is below 2^-48 |t|).
-// Then n ln2 (L0 + L1 + L2, n L0 exact) - log c (a float pair) + R + u.
+// Then n ln2 (a float pair from a table) - log c (a float pair) + R + u, the
+// leading parts by Fast2Sum: |n ln2| >= 0.69 > |log c| unless n = 0, and
+// |log c| >= 2^-11 > |R| unless c = 1 (a zero leading part makes the sum exact).
 // Also S0 = 1/z - 1 to 1x (c (1 + S) - 1), for the x1 term.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ ff log_newton_f(float dh, float dl, int n, float& S0) {
@@ -385,20 +387,19 @@ __device__ __forceinline__ ff log_newton_f(float dh, float dl, int n, float& S0)
     float tail = mul(mul(q.hi, R), fma_rn(fma_rn(R, -0x1.111112p-7f, 0x1.555556p-5f), R, -0x1.555556p-3f));
     ff Sh = fast_two_sum(-R, mul(0.5f, q.hi));
     float Sl = add(Sh.lo, fma_rn(0.5f, q.lo, tail));
-    // u = t + S + t S
-    ff a = two_sum(th, Sh.hi);
+    // u = t + S + t S: t + S is exact (Sterbenz: S is within a factor 2 of -t),
+    // and so is that plus RN(t S) (opposite, within a factor 2)
+    float a = add(th, Sh.hi);
     ff m = two_prod(th, Sh.hi);
-    float small = add(add(a.lo, m.lo), add(add(Sl, tl), fma_rn(tl, Sh.hi, mul(th, Sl))));
-    float u = add(add(a.hi, m.hi), small);  // a.hi + m.hi exact (opposite, within a factor 2)
+    float small = add(m.lo, add(add(Sl, tl), fma_rn(tl, Sh.hi, mul(th, Sl))));
+    float u = add(add(a, m.hi), small);
     // n ln2 - log c + R + u
-    ff s1 = two_sum(Lh, R);
-    float nf = (float)n;
-    ff s2 = fast_two_sum(mul(nf, TF_F_L0), s1.hi);  // n L0 exact; |n L0| >= 0.69 or n = 0
-    ff b2 = two_prod(nf, TF_F_L1);
-    ff c2 = two_sum(s2.hi, b2.hi);
-    float lo = add(add(add(s2.lo, c2.lo), fma_rn(nf, TF_F_L2, b2.lo)), add(add(s1.lo, Ll), u));
+    float2 nl = __ldg(reinterpret_cast<const float2*>(TF_FNLN2_TABLE) + (min(max(n, -160), 140) - TF_FNLN2_LO));
+    ff s1 = fast_two_sum(nl.x, Lh);
+    ff s2 = fast_two_sum(s1.hi, R);
+    float lo = add(add(s1.lo, s2.lo), add(add(nl.y, Ll), u));
     S0 = fma_rn(c, Sh.hi, cm1);
-    return fast_two_sum(c2.hi, lo);
+    return fast_two_sum(s2.hi, lo);
 }
 
 struct LogSplitF {

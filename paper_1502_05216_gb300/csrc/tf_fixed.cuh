@@ -55,6 +55,12 @@ __device__ __forceinline__ u128 shr128(u128 a) {
     }
 }
 
+// Logical shift left by a compile-time 0 < s < 64.
+template <int s>
+__device__ __forceinline__ u128 shl128(u128 a) {
+    return U(V(a) << s);
+}
+
 // Logical shift right by a run-time 0 <= s < 64.
 __device__ __forceinline__ u128 shr128_var(u128 a, int s) {
     uint64_t carry = (a.hi << 1) << (63 - s);  // a.hi << (64 - s), 0 for s == 0

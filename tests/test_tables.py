@@ -15,6 +15,7 @@ tables, a stride of the large ones), from the definitions stated in the kernels:
   TF_PX_E[m]        e^(2m) = E 2^e, E in [2^127, 2^128)
   TF_FLOGT[i]       {c = RN_float(2048/i), -log c as a float pair, c - 1}
   TF_FT / TF_FE[j]  2^(j/512) and 2^(j/512) - 1 as float pairs
+  TF_FNLN2[n]       n ln2 as a float pair, n = -160 .. 140
   TF_F_C0..C2       ln2/512 split, C0 with 7 bits;  TF_F_L0..L2  ln 2 split
 
 and replays three steps of the double kernels: the exp core's FP64 reduction
@@ -161,6 +162,12 @@ def test_float_tables():
             h, l = tab[j + 256]
             v = C.power(2, C.divide(D(j), 512)) - (1 if minus1 else 0)
             assert h == _f32(v) and abs(C.subtract(D(h) + D(l), v)) <= abs(v) * C.power(2, -47) + C.power(2, -160)
+    tab = _floats("TF_FNLN2_TABLE", 2)
+    assert len(tab) == 301 and int(_define("TF_FNLN2_LO").strip("()")) == -160
+    for n in range(-160, 141):
+        h, l = tab[n + 160]
+        v = D(n) * LN2
+        assert h == _f32(v) and abs(C.subtract(D(h) + D(l), v)) <= abs(v) * C.power(2, -48)
     tab = _floats("TF_FLOGT", 4)
     assert len(tab) == 1449
     for i in range(1448, 2897, 7):
