@@ -36,6 +36,8 @@ nearest, each with its unit):
   TF_HC68_m    1/(m+1)!, m = 3 .. 6, units 2^-68 (the 64-bit levels of the
       degree-6 H of the exp core).
   TF_C12FIX    ln2/65536 - C0 (> 0), units 2^-148: the tail of the reduction constant.
+  TF_CFIX136   ln2/65536, units 2^-136: the step that moves a negative reduced
+      argument of e^x to N - 1 and r + ln2/65536.
   TF_LN2FIX    ln2, units 2^-128 (the n ln2 term of the logarithm).
   TF_LOGT[i] for i = 724 .. 1448 (z = i/1024 covers [sqrt(1/2), sqrt(2))):
       {-log(c_i) in units 2^-128 as a two's complement (lo64, hi64), C_i, the
@@ -205,6 +207,7 @@ def main(out=sys.stdout):
     c12 = CTX.subtract(c, D(C0))
     assert c12 > 0 and fixed(c12, 148) < 2**106
     w(f"#define TF_C12FIX {{{u128(fixed(c12, 148))}}}\n\n")
+    w(f"#define TF_CFIX136 {{{u128(fixed(c, 136))}}}\n\n")
     w(f"#define TF_LN2FIX {{{u128(fixed(ln2, 128))}}}\n\n")
     w("/* coefficients (-1)^m/(m+1) of log1p(t)/t, units 2^-62, two's complement */\n")
     for m in range(0, 5):

@@ -8,6 +8,7 @@ tables, a stride of the large ones), from the definitions stated in the kernels:
   TF_TFIX_TABLE[j]  2^(j/65536) in units 2^-127 (round to nearest)
   TF_HC_m           1/(m+1)! in units 2^-127 (m <= 4) or 2^-72;  TF_HC68_m in units 2^-68
   TF_LN2FIX         ln 2 in units 2^-128;  TF_C0 + TF_C12FIX 2^-148 = ln2/65536
+  TF_CFIX136        ln2/65536 in units 2^-136
   TF_LG_m           (-1)^m / (m+1) in units 2^-62, m = 0 .. 4
   TF_LOG2T[j]       {-log c2_j in units 2^-128, C2_j = round(2^42 / (2^18 + j)), 0}
   TF_LOGT[i]        {-log c_i in units 2^-128, C_i = round(2^34 / i), c_i = C_i 2^-24 as a double}
@@ -88,6 +89,7 @@ def test_exp_table_and_constants():
     c0 = D(float.fromhex(_define("TF_C0")))
     c12 = C.multiply(D(_u128(_define("TF_C12FIX"))), C.power(2, -148))
     assert abs(C.subtract(C.add(c0, c12), C.divide(LN2, 65536))) < C.power(2, -148)
+    assert _u128(_define("TF_CFIX136")) == _fx(C.divide(LN2, 65536), 136)
     # C0 has at most 26 significant bits (N C0 exact for |N| < 2^27)
     assert (c0 * D(2) ** 42) == int(c0 * D(2) ** 42) and c0 * D(2) ** 42 < 2**26
     assert float.fromhex(_define("TF_INV_C")) == float(C.divide(65536, LN2))
@@ -189,7 +191,9 @@ def test_exp_reduction_is_exact():
     replayed with exact rationals: N = RN(x 65536/ln2) from the low word of
     fma(x, INV_C, 1.5 2^52), r0 = fma(-N, C0, x) is exactly x - N C0 (no
     rounding), and r = x - N ln2/65536 stays below 2^-17.52 for x over the
-    clamped range [-746, 710] (random, near the thresholds, tiny)."""
+    clamped range [-746, 710] (random, near the thresholds, tiny); e^x's
+    non-negative form (r + ln2/65536 at N - 1 for a negative r) lies in
+    [0, 2^-16.52)."""
     from fractions import Fraction
     inv_c = float.fromhex(_define("TF_INV_C"))
     c0 = float.fromhex(_define("TF_C0"))
@@ -208,13 +212,17 @@ def test_exp_reduction_is_exact():
         assert Fraction(r0) == Fraction(x) - Fraction(n) * Fraction(c0), x  # exact
         r = Fraction(x) - n * ln2_q / 65536
         assert abs(r) < Fraction(2) ** -17 * Fraction(0.6974), x  # 2^-17.52
+        # e^x's form (kPos): a negative r moves to N - 1 and r + ln2/65536
+        rp = r + ln2_q / 65536 if r < 0 else r
+        assert 0 <= rp < Fraction(2) ** -16 * Fraction(0.6974), x  # 2^-16.52
 
 
 def test_exp_core_H6_error_bound():
     """The exp core's degree-6 H(r) = (e^r - 1)/r (fx_H6) replayed bit for bit
     in Python integers (the same words, shifts and truncated products) for
-    |r| < 2^-17.52 of either sign, against the exact rational series: the
-    result, in units 2^-127, is within 2^-118 of H(r)."""
+    |r| < 2^-17.52 of either sign and for 0 <= r < 2^-16.52 (e^x's non-negative
+    reduction), against the exact rational series: the result, in units
+    2^-127, is within 2^-118 of H(r)."""
     from fractions import Fraction
     M64, M128 = (1 << 64) - 1, (1 << 128) - 1
     hc68 = {m: int(_define(f"TF_HC68_{m}").rstrip("ul").replace("0x", ""), 16) for m in range(3, 7)}
@@ -240,17 +248,16 @@ def test_exp_core_H6_error_bound():
         return addsub(hc[0], mulshift0(A8, H), neg)
 
     rng = np.random.default_rng(6)
-    top = int(2.0**-17.52 * 2.0**136)
-    As = [int(rng.integers(0, 1 << 62)) * (top >> 62) + int(rng.integers(0, 1 << 62)) for _ in range(3000)]  # below top
-    As += [0, 1, top - 1, top // 2, 1 << 100]
+    cases = []
+    for top, signs in ((int(2.0**-17.52 * 2.0**136), (False, True)), (int(2.0**-16.52 * 2.0**136), (False,))):
+        As = [int(rng.integers(0, 1 << 62)) * (top >> 62) + int(rng.integers(0, 1 << 62)) for _ in range(3000)]
+        cases += [(min(A, top - 1), neg) for A in As + [0, 1, top - 1, top // 2, 1 << 100] for neg in signs]
     worst = Fraction(0)
-    for A in As:
-        A = min(A, top - 1)
-        for neg in (False, True):
-            r = Fraction(-A if neg else A, 1 << 136)
-            exact = sum(r ** m / math.factorial(m + 1) for m in range(12))
-            got = Fraction(h6(A, neg), 1 << 127)
-            worst = max(worst, abs(got - exact))
+    for A, neg in cases:
+        r = Fraction(-A if neg else A, 1 << 136)
+        exact = sum(r ** m / math.factorial(m + 1) for m in range(12))
+        got = Fraction(h6(A, neg), 1 << 127)
+        worst = max(worst, abs(got - exact))
     assert worst < Fraction(1, 1 << 118), math.log2(worst)
 
 
