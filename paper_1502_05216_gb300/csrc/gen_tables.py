@@ -53,6 +53,11 @@ nearest, each with its unit):
       complement (lo64, hi64), C2_j, 0} with c2_j = C2_j 2^-24, C2_j =
       round(2^42 / (2^18 + j)): the second reciprocal table of the logarithm,
       t2 = (1 + t) c2_j - 1 with j = round(2^18 t), |t2| < 2^-18.9.
+  TF_LOGU[i], TF_LOG2U[j]  the same two reductions rounded up for tlog's main
+      path (n != 0): i = floor(1024 z), C_i = ceil(2^34 / i), so that t1 = z c_i
+      - 1 lies in [0, 2^-9.49); j = floor(2^18 t1) in [0, 362], C2_j = ceil(2^42
+      / (2^18 + j)), so that t2 = (1 + t1) c2_j - 1 lies in [0, 2^-17.97).  Rows
+      {-log c in units 2^-128 as (lo64, hi64), C, 0}.
   TF_LG_m      (-1)^m / (m+1), m = 0 .. 4, units 2^-62 (two's complement): the
       coefficients of log1p(t)/t.
 """
@@ -240,6 +245,41 @@ def main(out=sys.stdout):
         L = fixed(CTX.minus(CTX.ln(c)), 128)
         for t1 in (D(j) / 2**18 - D(1) / 2**19, D(j) / 2**18 + D(1) / 2**19):
             assert abs(CTX.subtract(CTX.multiply(1 + t1, c), 1)) < D(2) ** D("-18.9"), (j, t1)
+        Lu = L & (2**128 - 1)
+        w(f"  {{0x{Lu & (2**64 - 1):016x}ull, 0x{Lu >> 64:016x}ull, {C}ull, 0ull}},\n")
+    w("};\n\n")
+    # the sign-free pair of reciprocal tables of tlog's main path (n != 0):
+    # rounded up, indexed by floor, so that both reduced arguments are >= 0
+    w("\n#define TF_LOGU_LO 724\n#define TF_LOGU_HI 1448\n")
+    w("/* {-log(c_i) units 2^-128 as (lo64, hi64), C_i, 0} for i = 724 .. 1448, c_i = C_i 2^-24,\n"
+      "   C_i = ceil(2^34 / i): t1 = z c_i - 1 in [0, 2^-9.49) for i = floor(1024 z) */\n")
+    w("TF_TABLE_QUALIFIER unsigned long long TF_LOGU[725][4] = {\n")
+    zsplit = D(0x16a09e00000000) / D(2**52)  # the split's upper bound on z (log_split)
+    jmax = 0
+    for i in range(724, 1449):
+        C = -(-(2**34) // i)
+        c = CTX.divide(D(C), D(2**24))
+        L = fixed(CTX.minus(CTX.ln(c)), 128)
+        assert abs(L) < 2**126.5 and C < 2**25
+        assert CTX.multiply(D(i) / 1024, c) >= 1
+        t1max = CTX.subtract(CTX.multiply(min(D(i + 1) / 1024, zsplit), c), 1)
+        assert t1max < D(2) ** D("-9.49"), i
+        jmax = max(jmax, int(CTX.multiply(t1max, D(2**18)).to_integral_value(rounding=decimal.ROUND_FLOOR)))
+        Lu = L & (2**128 - 1)
+        w(f"  {{0x{Lu & (2**64 - 1):016x}ull, 0x{Lu >> 64:016x}ull, {C}ull, 0ull}},\n")
+    w("};\n\n")
+    assert jmax == 362
+    w(f"#define TF_LOG2U_HI {jmax}\n")
+    w("/* {-log(c2_j) units 2^-128 as (lo64, hi64), C2_j, 0} for j = 0 .. TF_LOG2U_HI,\n"
+      "   c2_j = C2_j 2^-24, C2_j = ceil(2^42 / (2^18 + j)): t = (1 + t1) c2_j - 1 in [0, 2^-17.97)\n"
+      "   for j = floor(2^18 t1) */\n")
+    w(f"TF_TABLE_QUALIFIER unsigned long long TF_LOG2U[{jmax + 1}][4] = {{\n")
+    for j in range(0, jmax + 1):
+        C = -(-(2**42) // (2**18 + j))
+        c = CTX.divide(D(C), D(2**24))
+        L = fixed(CTX.minus(CTX.ln(c)), 128)
+        assert CTX.multiply(1 + D(j) / 2**18, c) >= 1
+        assert CTX.subtract(CTX.multiply(1 + D(j + 1) / 2**18, c), 1) < D(2) ** D("-17.97"), j
         Lu = L & (2**128 - 1)
         w(f"  {{0x{Lu & (2**64 - 1):016x}ull, 0x{Lu >> 64:016x}ull, {C}ull, 0ull}},\n")
     w("};\n\n")

@@ -22,6 +22,10 @@ struct OpExp {
     static constexpr int min_blocks = 4;  // 64 registers: 32 warps per SM
     static constexpr double dummy = 0.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp1(a, b, z0, z1); }
+    __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
+                                 double& s1) {
+        tf::texp_pair(a0, b0, a1, b1, r0, r1, s0, s1);
+    }
 };
 struct OpExpm1 {
     static constexpr int min_blocks = 4;  // 64 registers: 32 warps per SM
@@ -32,6 +36,10 @@ struct OpLog {
     static constexpr int min_blocks = 4;  // 64 registers: 32 warps per SM
     static constexpr double dummy = 1.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1(a, b, z0, z1); }
+    __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
+                                 double& s1) {
+        tf::tlog_pair(a0, b0, a1, b1, r0, r1, s0, s1);
+    }
 };
 struct OpLog1p {
     static constexpr int threads = 128;   // 72 registers: 28 warps per SM
@@ -47,6 +55,12 @@ struct OpPExp {
     __device__ static void eval(double a, double b, double& z0, double& z1) {
         tf::texp_impl<true>(a, b, z0, z1);
         tf::couple(z0, z1);
+    }
+    __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
+                                 double& s1) {
+        tf::texp_pair(a0, b0, a1, b1, r0, r1, s0, s1);
+        tf::couple(r0, r1);
+        tf::couple(s0, s1);
     }
 };
 struct OpPExpm1 {
@@ -64,6 +78,12 @@ struct OpPLog {
         tf::tlog_impl<true>(a, b, z0, z1);
         tf::couple(z0, z1);
     }
+    __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
+                                 double& s1) {
+        tf::tlog_pair(a0, b0, a1, b1, r0, r1, s0, s1);
+        tf::couple(r0, r1);
+        tf::couple(s0, s1);
+    }
 };
 struct OpPLog1p {
     static constexpr double dummy = 0.0;
@@ -78,6 +98,10 @@ struct OpExpP {
     static constexpr double dummy = 0.0;
     static constexpr int min_blocks = 4;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp_impl<true, false>(a, b, z0, z1); }
+    __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
+                                 double& s1) {
+        tf::texp_pair<false>(a0, b0, a1, b1, r0, r1, s0, s1);
+    }
 };
 struct OpExpm1P {
     static constexpr double dummy = 0.0;
@@ -88,6 +112,10 @@ struct OpLogP {
     static constexpr double dummy = 1.0;
     static constexpr int min_blocks = 4;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog_impl<true, false>(a, b, z0, z1); }
+    __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
+                                 double& s1) {
+        tf::tlog_pair<false>(a0, b0, a1, b1, r0, r1, s0, s1);
+    }
 };
 struct OpLog1pP {
     static constexpr double dummy = 0.0;
@@ -99,12 +127,20 @@ struct OpExpTables {
     static constexpr double dummy = 0.0;
     static constexpr int min_blocks = 4;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp_impl<true, true, true>(a, b, z0, z1); }
+    __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
+                                 double& s1) {
+        tf::texp_pair<true, true>(a0, b0, a1, b1, r0, r1, s0, s1);
+    }
 };
 // The logarithms with the Newton step in binary64 (A/B variants of OpLog, OpLog1p).
 struct OpLogN64 {
     static constexpr int min_blocks = 4;
     static constexpr double dummy = 1.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog_impl<true, true, true>(a, b, z0, z1); }
+    __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
+                                 double& s1) {
+        tf::tlog_pair<true, true>(a0, b0, a1, b1, r0, r1, s0, s1);
+    }
 };
 struct OpLog1pN64 {
     static constexpr int threads = 128;
@@ -166,6 +202,19 @@ struct OpThreads<Op, decltype((void)Op::threads)> {
     static constexpr int value = Op::threads;
 };
 
+// Whether an op evaluates the two elements of a thread in one call (Op::eval2:
+// both main paths in straight-line code, so that their independent
+// instruction streams interleave; measured 11 % faster for tlog and 1.3 % for
+// texp at 64 registers, 6 % and 3 % slower at 78 registers and 24 warps).
+template <class Op, class = void>
+struct OpPair {
+    static constexpr bool value = false;
+};
+template <class Op>
+struct OpPair<Op, decltype((void)&Op::eval2)> {
+    static constexpr bool value = true;
+};
+
 // Unary, 2 elements per thread, 128-bit I/O.  Thread t covers elements 2t, 2t+1.
 template <class Op>
 __global__ void __launch_bounds__(OpThreads<Op>::value, Op::min_blocks) unary_v2(const double* x0, const double* x1,
@@ -189,8 +238,12 @@ __global__ void __launch_bounds__(OpThreads<Op>::value, Op::min_blocks) unary_v2
         b0 = x1 ? x1[i] : 0.0;
     }
     double r0, r1, s0, s1;
-    Op::eval(a0, b0, r0, r1);
-    Op::eval(a1, b1, s0, s1);
+    if constexpr (OpPair<Op>::value) {
+        Op::eval2(a0, b0, a1, b1, r0, r1, s0, s1);
+    } else {
+        Op::eval(a0, b0, r0, r1);
+        Op::eval(a1, b1, s0, s1);
+    }
     if (full) {
         st2(z0 + i, r0, s0);
         st2(z1 + i, r1, s1);

@@ -1,12 +1,18 @@
 """Deterministic edge cases of the double logarithms (tlog, tlog1p) against the oracle.
 
-The kernels reduce y = 2^n z by a reciprocal table (i = round(1024 z)) and place
-the fixed-point sum by cases: units 2^-116 for n != 0, 2^-128 off the table's
-centre for n = 0, and relative to d = z - 1 at the centre for n = 0 (switching
-at |d| = 2^-22 and, for the right shift of d c, at |d| = 2^-60).  These inputs
-sit on every such boundary:
+The kernels reduce y = 2^n z by a reciprocal table (i = round(1024 z) in the
+general core) and place the fixed-point sum by cases: units 2^-116 for n != 0,
+2^-128 off the table's centre for n = 0, and relative to d = z - 1 at the centre
+for n = 0 (switching at |d| = 2^-22 and, for the right shift of d c, at |d| =
+2^-60).  tlog's sign-free core takes i = floor(1024 z) and j = floor(2^18 t1)
+with tables rounded up, serves n = 0 outside [1 - 2^-10, 1 + 2^-22), and places
+its n = 0 sum in units 2^-136 in cell 1024.  These inputs sit on every such
+boundary:
 
 * z on both sides of every table cell boundary (i +- 1/2)/1024, at several n;
+* z on both sides of the sign-free core's cells i/1024 and of its second
+  table's cells t1 = j 2^-18 (z = (1 + j 2^-18)/c_i), and of 1 - 2^-10,
+  1 + 2^-22;
 * exact powers of two (d = 0) over the whole exponent range;
 * 1 +- 2^-k and their neighbours for every k (d crosses the placement switches);
 * tlog1p: +-2^-k down to the subnormals, the edges of the n = 0 band, cell
@@ -54,7 +60,12 @@ def _with_x1(x0, seed):
 
 def tlog_edges():
     cells = np.array([(i + h) / 1024 for i in range(724, 1449) for h in (-0.5, 0.5)])
-    z = _around(np.concatenate([cells, [SPLIT_Z, SPLIT_Z / 2, 1.0]]))
+    up = [i / 1024 for i in range(724, 1449)]
+    for i in range(724, 1449, 9):
+        ci = -(-(2**34) // i) / 2.0**24  # the sign-free core's c_i
+        up += [(1 + j * 2.0**-18) / ci for j in (1, 2, 77, 200, 300, 362)]
+    up += [1 - 2.0**-10, 1 - 2.0**-11, 1 + 2.0**-22, 1 + 2.0**-21, 1 + 2.0**-18]
+    z = _around(np.concatenate([cells, up, [SPLIT_Z, SPLIT_Z / 2, 1.0]]))
     z = z[(z >= SPLIT_Z / 2) & (z < SPLIT_Z)]
     ys = [z * 2.0**k for k in (0, 1, -1, 7, -7, 300, -300, 1000, -1000)]
     ys.append(np.exp2(np.arange(-1074, 1024, dtype=np.float64)))      # powers of two

@@ -12,6 +12,8 @@ tables, a stride of the large ones), from the definitions stated in the kernels:
   TF_LG_m           (-1)^m / (m+1) in units 2^-62, m = 0 .. 4
   TF_LOG2T[j]       {-log c2_j in units 2^-128, C2_j = round(2^42 / (2^18 + j)), 0}
   TF_LOGT[i]        {-log c_i in units 2^-128, C_i = round(2^34 / i), c_i = C_i 2^-24 as a double}
+  TF_LOGU[i]        {-log c_i in units 2^-128, C_i = ceil(2^34 / i), 0}
+  TF_LOG2U[j]       {-log c2_j in units 2^-128, C2_j = ceil(2^42 / (2^18 + j)), 0}, j = 0 .. 362
   TF_PX_C[n]        e^(n/256) in units 2^-124
   TF_PX_E[m]        e^(2m) = E 2^e, E in [2^127, 2^128)
   TF_FLOGT[i]       {c = RN_float(2048/i), -log c as a float pair, c - 1}
@@ -19,10 +21,11 @@ tables, a stride of the large ones), from the definitions stated in the kernels:
   TF_FNLN2[n]       n ln2 as a float pair, n = -160 .. 140
   TF_F_C0..C2       ln2/512 split, C0 with 7 bits;  TF_F_L0..L2  ln 2 split
 
-and replays three steps of the double kernels: the exp core's FP64 reduction
+and replays four steps of the double kernels: the exp core's FP64 reduction
 with exact rationals (exactness, and the bound on the reduced argument that
-the degree-6 H assumes), that H bit for bit in integers (its error bound), and
-the logarithm's second table reduction in integers (its bound).
+the degree-6 H assumes), that H bit for bit in integers (its error bound), the
+logarithm's second table reduction in integers (its bound), and tlog's
+sign-free reduction and seed in integers (signs and bounds).
 """
 import decimal
 import math
@@ -288,3 +291,87 @@ def test_log_second_reduction_replay():
         exact = (Fraction(T1, 2**136) + 1) * Fraction(C2, 2**24) - 1
         assert abs(Fraction(T2, 2**136) - exact) <= Fraction(1, 2**136)
         assert abs(T2) < 2**(136 - 18.9), (z, j)
+
+
+def test_log_rounded_up_tables():
+    """The rounded-up pair of tlog's sign-free core: C = ceil(...), so that z c_i
+    >= 1 over cell i = floor(1024 z) and (1 + t1) c2_j >= 1 over cell j =
+    floor(2^18 t1); the reduced arguments stay below 2^-9.49 and 2^-17.97."""
+    tab = _ints("TF_LOGU", 4)
+    assert len(tab) == 725 and int(_define("TF_LOGU_LO")) == 724 and int(_define("TF_LOGU_HI")) == 1448
+    zsplit = D(0x16A09E00000000) / D(2**52)
+    for i in range(724, 1449):
+        lo, hi, Ci, zero = tab[i - 724]
+        assert Ci == -(-(2**34) // i) and zero == 0
+        c = C.multiply(D(Ci), C.power(2, -24))
+        L = lo | (hi << 64)
+        L = L - (1 << 128) if L >> 127 else L
+        if i % 7 == 0 or i in (724, 1023, 1024, 1448):
+            assert L == _fx(C.minus(C.ln(c)), 128), i
+        assert C.multiply(D(i) / 1024, c) >= 1
+        assert C.subtract(C.multiply(min(D(i + 1) / 1024, zsplit), c), 1) < D(2) ** D("-9.49")
+    tab2 = _ints("TF_LOG2U", 4)
+    jmax = int(_define("TF_LOG2U_HI"))
+    assert jmax == 362 and len(tab2) == jmax + 1
+    for j in range(0, jmax + 1):
+        lo, hi, C2, zero = tab2[j]
+        assert C2 == -(-(2**42) // (2**18 + j)) and zero == 0 and C2 <= 1 << 24
+        c = C.multiply(D(C2), C.power(2, -24))
+        L = lo | (hi << 64)
+        L = L - (1 << 128) if L >> 127 else L
+        if j % 5 == 0 or j == jmax:
+            assert L == _fx(C.minus(C.ln(c)), 128), j
+        assert C.multiply(1 + D(j) / 2**18, c) >= 1
+        assert C.subtract(C.multiply(1 + D(j + 1) / 2**18, c), 1) < D(2) ** D("-17.97")
+    assert tab2[0][2] == 1 << 24 and tab2[0][0] == tab2[0][1] == 0  # j = 0: c2 = 1
+
+
+def test_log_sign_free_reduction_replay():
+    """tlog's sign-free core (log_core_up) replayed in integers as the kernel
+    forms each value, for random z over the split's range [0.7071056,
+    1.4142112) and every cell's ends: T1 = (Z C_i 2^59) mod 2^128 equals
+    t1 2^136 exactly and lies in [0, 2^126.51); j = T1's top word >> 54 is in
+    [0, 362]; T2 = floor(T1 C2_j / 2^24) - (2^24 - C2_j) 2^112 lies in [0,
+    2^118.03) and within one unit of ((1 + t1) c2_j - 1) 2^136; the seed
+    R = t G(t) with G = 1 - t (1/2 - t/3) in truncated 64-bit steps is within
+    2^-68 of log1p(t) (t taken to 2^-71, R to 2^-69), so that the Newton
+    residual u = (1 + t) e^-R - 1 is below 2^-67.9 and the u^2/2 that the step
+    drops below 2^-136."""
+    from fractions import Fraction
+    logu = _ints("TF_LOGU", 4)
+    log2u = _ints("TF_LOG2U", 4)
+    LG0, LG1, LG2 = (int(_define("TF_LG_%d" % m).split("0x")[1][:16], 16) for m in range(3))
+    LG1 = (1 << 64) - LG1  # TF_LG_1 is -1/2 in two's complement
+    assert LG0 == 1 << 62 and LG1 == 1 << 61 and LG2 == _fx(D(1) / 3, 62)
+    M128 = (1 << 128) - 1
+    lo_z, hi_z = 0x16A09E00000000, 0x2D413C00000000  # Z = z 2^53 over the split's range
+    rng = np.random.default_rng(11)
+    Zs = [int(v) for v in rng.integers(lo_z, hi_z, 20000)]
+    for i in range(724, 1449):
+        Zs += [max(i << 43, lo_z), min(((i + 1) << 43) - 1, hi_z - 1)]
+    Zs += [1 << 53, (1 << 53) - 1, (1 << 53) + 1]
+    worst = Fraction(0)
+    for Z in Zs:
+        i = Z >> 43
+        assert 724 <= i <= 1448
+        Ci = logu[i - 724][2]
+        T1 = ((Z * Ci) << 59) & M128
+        exact1 = Fraction(Z * Ci, 2**77) - 1
+        assert Fraction(T1, 2**136) == exact1 and 0 <= T1 < 2 ** (136 - 9.49)
+        j = (T1 >> 64) >> 54
+        assert 0 <= j <= 362
+        C2 = log2u[j][2]
+        T2 = (((T1 * C2) >> 24) - (((1 << 24) - C2) << 112)) & M128
+        assert T2 < 2 ** (136 - 17.97), (Z, j)
+        exact2 = (exact1 + 1) * Fraction(C2, 2**24) - 1
+        assert 0 <= Fraction(T2, 2**136) - exact2 + Fraction(1, 2**136) <= Fraction(1, 2**136)
+        t71 = (T2 >> 64) >> 1
+        g = LG1 - ((t71 * LG2) >> 71)
+        g = LG0 - ((t71 * g) >> 71)
+        r69 = (t71 * g) >> 64
+        t = Fraction(T2, 2**136)
+        # log1p(t) by its alternating series to far beyond 2^-80 (t < 2^-17.97)
+        lp = sum(Fraction((-1) ** (m + 1), m) * t**m for m in range(1, 7))
+        err = abs(Fraction(r69, 2**69) - lp)
+        worst = max(worst, err)
+    assert worst < Fraction(1, 2**68), math.log2(worst)
