@@ -580,6 +580,39 @@ __device__ __forceinline__ void tlogf_impl(float y0, float y1, float& z0, float&
     z1 = nanres ? nan : z1;
 }
 
+// The four elements of a thread in one call, for the float kernel's four
+// elements per thread: one vote on special inputs for all four; a warp without
+// any runs the four main paths in straight-line code, then one vote on rare
+// lanes; any other warp runs tlogf_impl for each.  Results are those of
+// tlogf_impl, bit for bit (measured 4 % faster at 2^28; the same form for
+// texpf was 2 % slower and is not used).
+__device__ __forceinline__ void tlogf_quad(const float (&y0)[4], const float (&y1)[4], float (&z0)[4], float (&z1)[4]) {
+    bool special = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) special |= !((y0[q] >= 0x1p-126f) & (y0[q] < kInf)) | !(fabsf(y1[q]) < kInf);
+    if (__any_sync(0xffffffffu, special)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tlogf_impl<true>(y0[q], y1[q], z0[q], z1[q]);
+        return;
+    }
+    bool rare[4], anyrare = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        LogSplitF s = log_split_f<false>(y0[q]);
+        float S0;
+        ff L = log_newton_f(sub(s.z, 1.0f), 0.0f, s.n, S0);
+        z0[q] = L.hi;
+        z1[q] = add_log1p_ratio(mul(y1[q], s.inv), S0, L.lo);
+        rare[q] = loose(y1[q], y0[q]);
+        anyrare |= rare[q];
+    }
+    if (__any_sync(0xffffffffu, anyrare)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (rare[q]) tlogf_rare(y0[q], y1[q], z0[q], z1[q]);
+    }
+}
+
 static __device__ __noinline__ void tlog1pf_rare(float y1, ff w, float z0, float& z1) {
     if (absbits(y1) >= kExpMask) {
         z1 = (absbits(y1) > kExpMask) ? y1 : ((y1 > 0.0f) ? y1 : __int_as_float(0x7fc00000));
