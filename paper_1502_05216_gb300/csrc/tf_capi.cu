@@ -29,7 +29,8 @@ struct OpExp {
     }
 };
 struct OpExpm1 {
-    static constexpr int min_blocks = 4;  // 64 registers: 32 warps per SM
+    static constexpr int threads = 128;   // 72 registers, no spills: 28 warps per SM (at 64 it
+    static constexpr int min_blocks = 7;  // spilled 16 bytes and ran the 2^24 hard cases 2.4 % slower)
     static constexpr double dummy = 0.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texpm11(a, b, z0, z1); }
 };
@@ -52,7 +53,8 @@ struct OpLog1p {
 // arguments (texpp, texpm1p, tlogp, tlog1pp).
 struct OpPExp {
     static constexpr double dummy = 0.0;
-    static constexpr int min_blocks = 4;
+    static constexpr int threads = 128;  // as OpExp
+    static constexpr int min_blocks = 9;
     __device__ static void eval(double a, double b, double& z0, double& z1) {
         tf::texp_impl<true>(a, b, z0, z1);
         tf::couple(z0, z1);
@@ -66,7 +68,8 @@ struct OpPExp {
 };
 struct OpPExpm1 {
     static constexpr double dummy = 0.0;
-    static constexpr int min_blocks = 4;
+    static constexpr int threads = 128;  // as OpExpm1
+    static constexpr int min_blocks = 7;
     __device__ static void eval(double a, double b, double& z0, double& z1) {
         tf::texpm1_impl<true>(a, b, z0, z1);
         tf::couple(z0, z1);
@@ -97,7 +100,8 @@ struct OpPLog1p {
 };
 struct OpExpP {
     static constexpr double dummy = 0.0;
-    static constexpr int min_blocks = 4;
+    static constexpr int threads = 128;  // as OpExp
+    static constexpr int min_blocks = 9;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp_impl<true, false>(a, b, z0, z1); }
     __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
                                  double& s1) {
@@ -106,7 +110,8 @@ struct OpExpP {
 };
 struct OpExpm1P {
     static constexpr double dummy = 0.0;
-    static constexpr int min_blocks = 4;
+    static constexpr int threads = 128;  // as OpExpm1
+    static constexpr int min_blocks = 7;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texpm1_impl<true, false>(a, b, z0, z1); }
 };
 struct OpLogP {
@@ -126,7 +131,8 @@ struct OpLog1pP {
 };
 struct OpExpTables {
     static constexpr double dummy = 0.0;
-    static constexpr int min_blocks = 4;
+    static constexpr int threads = 128;  // as OpExp
+    static constexpr int min_blocks = 9;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp_impl<true, true, true>(a, b, z0, z1); }
     __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
                                  double& s1) {
@@ -199,8 +205,9 @@ __device__ __forceinline__ void st2(double* p, double a, double b) {
 
 // Block size of an op's vector kernel: Op::threads where the op sets it, else
 // kThreads.  With min_blocks it sets the register budget: 256 x 4 blocks gives
-// 64 registers (32 warps per SM); 128 x 7 gives 72 (28 warps), which the
-// two-table log of tlog1p needs to run without spills.
+// 64 registers (32 warps per SM: tlog); 128 x 9 gives 56 (36 warps: texp);
+// 128 x 7 gives 72 (28 warps), which the two-table log of tlog1p and texpm1
+// need to run without spills.
 template <class Op, class = void>
 struct OpThreads {
     static constexpr int value = kThreads;
