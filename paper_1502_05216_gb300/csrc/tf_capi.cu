@@ -35,7 +35,8 @@ struct OpExpm1 {
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texpm11(a, b, z0, z1); }
 };
 struct OpLog {
-    static constexpr int min_blocks = 4;  // 64 registers: 32 warps per SM
+    static constexpr int threads = 128;   // 72 registers, no spills: 28 warps per SM (1.2 % faster
+    static constexpr int min_blocks = 7;  // than at 64 with 20 bytes of spills)
     static constexpr double dummy = 1.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog1(a, b, z0, z1); }
     __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
@@ -77,7 +78,8 @@ struct OpPExpm1 {
 };
 struct OpPLog {
     static constexpr double dummy = 1.0;
-    static constexpr int min_blocks = 4;
+    static constexpr int threads = 128;  // as OpLog
+    static constexpr int min_blocks = 7;
     __device__ static void eval(double a, double b, double& z0, double& z1) {
         tf::tlog_impl<true>(a, b, z0, z1);
         tf::couple(z0, z1);
@@ -116,7 +118,8 @@ struct OpExpm1P {
 };
 struct OpLogP {
     static constexpr double dummy = 1.0;
-    static constexpr int min_blocks = 4;
+    static constexpr int threads = 128;  // as OpLog
+    static constexpr int min_blocks = 7;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog_impl<true, false>(a, b, z0, z1); }
     __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
                                  double& s1) {
@@ -131,8 +134,7 @@ struct OpLog1pP {
 };
 struct OpExpTables {
     static constexpr double dummy = 0.0;
-    static constexpr int threads = 128;  // as OpExp
-    static constexpr int min_blocks = 9;
+    static constexpr int min_blocks = 4;  // 64 registers (at 56 it spilled and ran 2.5 % slower)
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::texp_impl<true, true, true>(a, b, z0, z1); }
     __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
                                  double& s1) {
@@ -141,7 +143,8 @@ struct OpExpTables {
 };
 // The logarithms with the Newton step in binary64 (A/B variants of OpLog, OpLog1p).
 struct OpLogN64 {
-    static constexpr int min_blocks = 4;
+    static constexpr int threads = 128;  // as OpLog
+    static constexpr int min_blocks = 7;
     static constexpr double dummy = 1.0;
     __device__ static void eval(double a, double b, double& z0, double& z1) { tf::tlog_impl<true, true, true>(a, b, z0, z1); }
     __device__ static void eval2(double a0, double b0, double a1, double b1, double& r0, double& r1, double& s0,
@@ -205,9 +208,9 @@ __device__ __forceinline__ void st2(double* p, double a, double b) {
 
 // Block size of an op's vector kernel: Op::threads where the op sets it, else
 // kThreads.  With min_blocks it sets the register budget: 256 x 4 blocks gives
-// 64 registers (32 warps per SM: tlog); 128 x 9 gives 56 (36 warps: texp);
-// 128 x 7 gives 72 (28 warps), which the two-table log of tlog1p and texpm1
-// need to run without spills.
+// 64 registers (32 warps per SM); 128 x 9 gives 56 (36 warps: texp); 128 x 7
+// gives 72 (28 warps), which tlog, tlog1p's two-table log and texpm1 need to
+// run without spills.
 template <class Op, class = void>
 struct OpThreads {
     static constexpr int value = kThreads;
