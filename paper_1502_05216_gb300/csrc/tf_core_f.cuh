@@ -552,7 +552,13 @@ static __device__ __noinline__ float log_deviation_f(float v0, float v1, float v
     if (v.hi == 0.0f) return -__int_as_float(0x7f800000);
     LogOutF o = log_pos_f(v.hi, huge ? 1 : 0);
     float q = mul(mul(v.lo, o.sub), o.inv);
-    return add(sub(o.L.hi, z0), add(o.L.lo, fma_rn(q, o.S0, q)));
+    // G = (L.hi - z0) + L.lo + t with t = q (1 + S0) = v.lo / v.hi: L.hi - z0
+    // exactly as a pair and its leading part summed with q exactly, then one
+    // final rounding (L.hi may be far from z0, where a rounded L.hi - z0 alone
+    // would cost up to another half ulp of the result)
+    ff d = two_sum(o.L.hi, -z0);
+    ff e = two_sum(d.hi, q);
+    return add(e.hi, add(e.lo, fma_rn(q, o.S0, add(o.L.lo, d.lo))));
 }
 
 static __device__ __noinline__ void tlogf_rare(float y0, float y1, float z0, float& z1) {

@@ -99,6 +99,40 @@ def test_misaligned_equals_aligned_f32(tf, func):
     assert np.array_equal(o1[1:].cpu().numpy().view(np.int32), ref[1].view(np.int32))
 
 
+@pytest.mark.parametrize("func", UNARY)
+def test_mixed_warps_equal_scalar_kernel_f32(tf, func):
+    """The vector kernel evaluates a thread's four elements in calls of two
+    (texpf) or four (tlogf) with warp-wide votes choosing the form, or one after
+    the other; the scalar kernel evaluates each element alone.  With a special
+    value every 97 elements (in x0 or x1) and, for the logarithms, a y0 next to
+    1 every 53, most warps mix both kinds of lanes: same bits, and the oracle's
+    bar."""
+    import torch
+    n = 4099
+    x0, x1 = (a.copy() for a in I.workload_f32(func, n))
+    sp = I.SPECIALS_F.astype(np.float32)
+    idx = np.arange(5, n, 97)
+    x0[idx[::2]] = sp[np.arange(idx[::2].size) % sp.size]
+    x1[idx[1::2]] = sp[np.arange(idx[1::2].size) % sp.size]
+    if func in ("tlog", "tlog1p"):
+        near = np.arange(11, n, 53)
+        u = I.uniform(43, 1, near.size)
+        x0[near] = ((1.0 + (u - 0.5) * 2.0**-9) - (1.0 if func == "tlog1p" else 0.0)).astype(np.float32)
+    ref = run(tf, func, x0, x1)
+    bufs = []
+    for a in (x0, x1):
+        b = torch.zeros(n + 1, dtype=torch.float32, device="cuda:0")
+        b[1:] = torch.from_numpy(a).cuda()
+        bufs.append(b[1:])
+    o0 = torch.zeros(n + 1, dtype=torch.float32, device="cuda:0")
+    o1 = torch.zeros(n + 1, dtype=torch.float32, device="cuda:0")
+    tf.FUNCS_F[func](bufs[0], bufs[1], out=(o0[1:], o1[1:]))
+    torch.cuda.synchronize()
+    assert np.array_equal(o0[1:].cpu().numpy().view(np.int32), ref[0].view(np.int32))
+    assert np.array_equal(o1[1:].cpu().numpy().view(np.int32), ref[1].view(np.int32))
+    check(tf, func, x0, x1, f"{func}f mixed warps", rate=1.0)
+
+
 @pytest.mark.parametrize("func", ("texp", "tlog"))
 def test_full_size_sampled_f32(tf, func):
     """n = 2^28 floats (the precision-tier size), every 2^11-th element and the

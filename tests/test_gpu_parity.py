@@ -125,6 +125,48 @@ def test_misaligned_equals_aligned(tf, func):
     assert o0[0].item() == 0 and o1[0].item() == 0
 
 
+def _sprinkled(func, n, seed):
+    """The workload with a special value every 97 elements (cycling through the
+    IEEE specials, in x0 or x1) and, for the logarithms, a y0 next to 1 every 53:
+    most warps mix the lanes of the kernels' straight-line paths with lanes
+    that send the whole warp to the per-element form."""
+    x0, x1 = (a.copy() for a in I.workload(func, n))
+    sp = I.SPECIALS
+    idx = np.arange(5, n, 97)
+    x0[idx[::2]] = sp[np.arange(idx[::2].size) % sp.size]
+    x1[idx[1::2]] = sp[np.arange(idx[1::2].size) % sp.size]
+    if func in ("tlog", "tlog1p"):
+        near = np.arange(11, n, 53)
+        u = I.uniform(seed, 1, near.size)
+        x0[near] = (1.0 + (u - 0.5) * 2.0**-9) - (1.0 if func == "tlog1p" else 0.0)
+    return x0, x1
+
+
+@pytest.mark.parametrize("func", UNARY)
+def test_mixed_warps_equal_scalar_kernel(tf, func):
+    """The vector kernel evaluates a thread's two elements in one call (texp,
+    tlog) or one after the other, with warp-wide votes choosing the form; the
+    scalar kernel (pointers not 16-byte aligned) evaluates each element alone.
+    On warps that mix special, rare and ordinary lanes both give the same bits,
+    and match the oracle."""
+    import torch
+    n = 4099
+    args = _sprinkled(func, n, 41)
+    ref0, ref1 = run(tf, func, *args)
+    bufs = []
+    for a in args:
+        b = torch.zeros(n + 1, dtype=torch.float64, device="cuda:0")
+        b[1:] = torch.from_numpy(a).to("cuda:0")
+        bufs.append(b[1:])
+    o0 = torch.zeros(n + 1, dtype=torch.float64, device="cuda:0")
+    o1 = torch.zeros(n + 1, dtype=torch.float64, device="cuda:0")
+    tf.FUNCS[func](*bufs, out=(o0[1:], o1[1:]))
+    torch.cuda.synchronize()
+    assert np.array_equal(o0[1:].cpu().numpy().view(np.int64), ref0.view(np.int64))
+    assert np.array_equal(o1[1:].cpu().numpy().view(np.int64), ref1.view(np.int64))
+    check(tf, func, args, f"{func} mixed warps", rate=1.0)
+
+
 @pytest.mark.parametrize("func", UNARY)
 def test_in_place(tf, func):
     """z0 may alias x0 and z1 may alias x1."""
