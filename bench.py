@@ -279,17 +279,20 @@ class Clocks:
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------------
 
-def oracle_rate(budget_s: float, per_func_cap: int = 1 << 22, funcs=METRIC_FUNCS):
+def oracle_rate(budget_s: float, per_func_cap: int = 1 << 26, funcs=METRIC_FUNCS):
     """Time the CPU oracle on a bounded sample of the metric's functions'
-    workloads (texp and tlog): elements/s over all host threads, plus the
-    sample description."""
+    workloads (texp and tlog), sized from a probe to take about budget_s:
+    elements/s over all host threads, plus the sample description."""
     import oracle
     from paper_1502_05216_gb300 import inputs as I
     lib = oracle.load()
-    probe = 1 << 13
+    probe = 1 << 16
+    pargs = {f: I.workload(f, probe) for f in funcs}
+    for f in funcs:  # warm-up: library load and thread start
+        oracle.evaluate(f, *pargs[f], lib=lib)
     t0 = time.perf_counter()
     for f in funcs:
-        oracle.evaluate(f, *I.workload(f, probe), lib=lib)
+        oracle.evaluate(f, *pargs[f], lib=lib)
     rate0 = len(funcs) * probe / (time.perf_counter() - t0)
     m = int(min(per_func_cap, max(probe, budget_s * rate0 / len(funcs))))
     args = {f: I.workload(f, m, start=1 << 30) for f in funcs}
