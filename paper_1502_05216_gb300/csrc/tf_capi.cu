@@ -1,11 +1,12 @@
 // tf_capi.cu -- elementwise twofold kernels for sm_103a and the C ABI of include/tf.h.
 //
 // One thread evaluates two consecutive elements (two independent chains of
-// FP64 work for the scheduler) and moves them with 128-bit loads and stores
-// when every pointer is 16-byte aligned.  All 32 lanes of a warp always run
-// the element code -- lanes past the end work on a harmless dummy argument and
-// store nothing -- so that the warp-uniform votes (__any_sync) that guard the
-// rare special-case paths see a full warp.
+// FP64 work for the scheduler; texp and tlog take both in one straight-line
+// call, OpPair) and moves them with 128-bit loads and stores when every pointer
+// is 16-byte aligned (four elements per thread for float twofolds).  All 32
+// lanes of a warp always run the element code -- lanes past the end work on a
+// harmless dummy argument and store nothing -- so that the warp-uniform votes
+// (__any_sync) that guard the rare special-case paths see a full warp.
 #include <cuda_runtime.h>
 
 #include <cstdint>
